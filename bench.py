@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the DP-AVF2 checkerboard solver (arXiv 2502.09537) on one B300.
+
+Workload (default): the 2D KGS problem on [-20,20)^2 with N = 2048^2 points,
+kappa1 = kappa2 = mu = gamma = 1, tau = 1e-3, 1000 DP-AVF2 steps in float64,
+psi0 = (1+i) exp(-r^2), u0 = exp(-r^2), v0 = 0 plus seeded Gaussian noise
+(sigma 1e-4); the discrete energy is evaluated every 100 steps.  One benchmark
+step = one such solve: load the initial state (already in HBM), 1000 steps,
+10 energy/mass evaluations.  Metric: grid-point updates per second
+(N^d x steps / time).  Multi-GPU: every rank solves its own instance (the
+instances are independent), value = all ranks' point-updates / max time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload 2d|1d|3d] [--precision fp64|fp32]
+
+The reference arm (--impl reference) times the CPU oracle (oracle/, the
+OpenMP checkerboard twin, bitwise equal to the serial oracle) on the host's
+cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "point-updates/s & %HBM roofline, FP64 vs FP32 @stated err; serve p50/p99 latency"
+UNIT = "point-updates/s"
+ENERGY_EVERY = 100
+
+
+def flops_per_point_update(dim: int) -> float:
+    """Algorithmic flops of one point-update (one point, one full DP-AVF2 step)
+    in the fused colour-pass formulation (kgs_point.cuh), FMA = 2, add/mul/
+    reciprocal = 1: neighbour sums 3(2d-1); black pass 2 x (r 2 + 1/(1+r^2) 3
+    + Psi 15) + t 6 + 2 x (U,V) 10 = 66; red pass t 6 + (U,V) 10 + r 2 +
+    1/(1+r^2) 3 + 2 x Psi 15 + t 6 + (U,V) 10 = 67; mean over the colours."""
+    return 3 * (2 * dim - 1) + 66.5
+
+
+def bytes_per_point_update(elem: int) -> int:
+    """Algorithmic HBM bytes of one point-update: read and write the four
+    fields once (the two colour passes of a step each touch their own half)."""
+    return 2 * 4 * elem
+
+
+def make_workload(name: str):
+    from paper_2502_09537_b300 import inputs
+    if name == "2d":
+        return inputs.gauss_2d(2048, 1000)
+    if name == "1d":
+        return inputs.soliton_1d(512, 2000)
+    if name == "3d":
+        return inputs.gauss_3d(512, 200)
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(work, seconds_target: float = 12.0):
+    """The oracle (OpenMP checkerboard twin, all host cores) on a bounded
+    sample of the workload: the full grid for a few steps."""
+    import oracle
+    threads = oracle.max_threads()
+    st = tuple(np.array(a, copy=True) for a in work.state)
+    t0 = time.perf_counter()
+    oracle.steps_checkerboard_omp(work.prob, *st, 1, threads)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(work.nsteps, int(seconds_target / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.steps_checkerboard_omp(work.prob, *st, n, threads)
+    dt = time.perf_counter() - t0
+    return {"value": work.prob.points * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{work.name}: full grid, {n} of {work.nsteps} steps "
+                      f"(OpenMP checkerboard twin, bitwise equal to the serial oracle)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    work = make_workload(args.workload)
+    threads = oracle.max_threads()
+    st = tuple(np.array(a, copy=True) for a in work.state)
+    t0 = time.perf_counter()
+    oracle.steps_checkerboard_omp(work.prob, *st, 1, threads)
+    t1 = max(time.perf_counter() - t0, 1e-6)
+    per_step = max(1, min(work.nsteps, int(4.0 / t1)))
+    times = []
+    for k in range(args.warmup + args.steps):
+        st = tuple(np.array(a, copy=True) for a in work.state)
+        t0 = time.perf_counter()
+        oracle.steps_checkerboard_omp(work.prob, *st, per_step, threads)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = work.prob.points * per_step * len(times) / total
+    sample = (f"{work.name}: full grid, {per_step} of {work.nsteps} steps per timed step "
+              f"(OpenMP checkerboard twin, bitwise equal to the serial oracle)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": work.name, "dim": work.prob.dim, "N": work.prob.N,
+                   "steps_per_solve": work.nsteps, "precision": "fp64", "sample_steps": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def solve(s, stream, init, nsteps, per_chunk_events=None):
+    """One benchmark step: load the initial state, nsteps DP-AVF2 steps with the
+    energy evaluated every ENERGY_EVERY steps.  Returns the invariants seen."""
+    s.set_state(*init, stream=stream)
+    seen = [s.invariants(stream=stream)]
+    done = 0
+    while done < nsteps:
+        n = min(ENERGY_EVERY, nsteps - done)
+        if per_chunk_events is not None:
+            a, b = per_chunk_events.pop(0)
+            a.record(stream)
+            s.step(n, stream=stream)
+            b.record(stream)
+        else:
+            s.step(n, stream=stream)
+        done += n
+        seen.append(s.invariants(stream=stream))
+    return seen
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2502_09537_b300 import build as kbuild
+    from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, Solver, probe_fma_rate
+    kbuild.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    work = make_workload(args.workload)
+    prob = work.prob
+    precision = KGS_FP64 if args.precision == "fp64" else KGS_FP32
+    elem = 8 if precision == KGS_FP64 else 4
+    stream = torch.cuda.Stream()
+    init_dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in work.state]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    nchunks = (work.nsteps + ENERGY_EVERY - 1) // ENERGY_EVERY
+    s = Solver.from_problem(prob, precision)
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            solve(s, stream, init_dev, work.nsteps)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        iter_ms, kern_ms = [], []
+        launches0 = s.launch_count
+        drift = 0.0
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(nchunks)]
+                kev = list(ev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                seen = solve(s, stream, init_dev, work.nsteps, per_chunk_events=kev)
+                e1.record(stream)
+                stream.synchronize()
+                iter_ms.append(e0.elapsed_time(e1))
+                kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+                E0, S0, _ = seen[0]
+                drift = max(drift, max(abs(E - E0) / max(S0, S) for E, S, _ in seen))
+        launches = s.launch_count - launches0
+    total_ms = sum(iter_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pts_per_step = prob.points * work.nsteps
+    value = world * pts_per_step * args.steps / (total_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned)
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in work.state]
+    host_out = [torch.empty(a.shape, dtype=torch.float64).pin_memory().numpy() for a in work.state]
+    with torch.cuda.stream(stream):
+        e2e_ms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            solve(s, stream, host_in, work.nsteps)
+            s.get_state(host_out, stream=stream)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = world * pts_per_step * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
+
+    # roofline of the dominant kernel: the fused colour pass
+    passes_per_chunk = 2 * ENERGY_EVERY + 1
+    pass_ms = sum(kern_ms) / (args.steps * nchunks * passes_per_chunk)
+    peaks = measured_peaks()
+    if precision == KGS_FP64:
+        fma_rate, _ = probe_fma_rate(64, 2048, 8, stream)
+        flops_per_launch = prob.points / 2 * flops_per_point_update(prob.dim)
+        achieved = flops_per_launch / (pass_ms * 1e-3) / 1e12
+        peak = 2 * fma_rate / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured FP64 FMA rate x 2 (kgs_probe_fma_rate, same run)",
+                "flops_per_point_update": flops_per_point_update(prob.dim),
+                "hbm_frac": bytes_per_point_update(elem) * prob.points / 2 / (pass_ms * 1e-3)
+                / 1e9 / peaks.get("hbm_gbs", 6400.0)}
+    else:
+        bytes_per_launch = prob.points / 2 * bytes_per_point_update(elem)
+        achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6400.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
+        "data": "synthetic",
+        "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
+                   "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
+                   "energy_every": ENERGY_EVERY,
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"{world} independent instance(s), one per GPU"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * prob.points * 8, "d2h_bytes_per_step": 4 * prob.points * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "energy_drift": drift,
+        "pass_ms": pass_ms,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(work)
+    s.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

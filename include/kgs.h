@@ -1,0 +1,148 @@
+/*
+ * kgs.h -- C ABI of libkgs: the DP-AVF2 checkerboard solver for the periodic
+ * Klein-Gordon-Schroedinger equations on a B300 GPU (sm_103a).
+ *
+ * The method (arXiv 2502.09537):
+ *   i psi_t + (kappa1/2) Lap psi + gamma u psi = 0,
+ *   u_tt - kappa2 Lap u + mu^2 u - gamma |psi|^2 = 0            (Eq. kgs, Sec. 1)
+ * on the periodic box [-L/2, L/2)^d, d in {1,2,3}, discretised by central
+ * differences on N points per direction, h = L/N (Sec. 2, Eq. kgs-semi), and
+ * advanced by DP-AVF2 = Phi*_{tau/2} o Phi_{tau/2} (Eq. dp-comp): the explicit
+ * pointwise base update of Eq. scheme1 and its adjoint (Eq. dp-avf-kj-adj),
+ * swept in the checkerboard order of Sec. 4.2 / Algorithm 3 (red = points whose
+ * 1-based index sum is odd; base half red then black, adjoint half black then
+ * red).  The scheme conserves the discrete energy E_h exactly (Thm. 3.1).
+ *
+ * State layout seen by callers: four float64 arrays P = Re psi, Q = Im psi,
+ * U = u, V = u_t, each of N^d elements in C order with shape (N,)*d and index
+ * [ix][iy][iz] (z fastest), the paper's linear index i = (j-1)N + k (Sec. 2).
+ * Grid point [ix][iy][iz] sits at (-L/2 + ix h, -L/2 + iy h, -L/2 + iz h).
+ *
+ * Ownership: the library owns every device buffer of a handle (allocated in
+ * kgs_create*, freed in kgs_destroy).  Caller buffers passed to kgs_set_state /
+ * kgs_get_state are never retained.
+ *
+ * Streams: every `stream` argument is a cudaStream_t passed as void*; NULL is
+ * the legacy default stream.  Calls that take device buffers are asynchronous
+ * on that stream; calls that take host buffers or return host values
+ * synchronise it before returning.  kgs_energy and kgs_mass run on the stream
+ * of the handle's latest kgs_set_state / kgs_step call.
+ *
+ * Threading: a handle is not thread-safe; distinct handles are independent.
+ * Errors: functions return KGS_OK (0) or a negative status.  kgs_last_error()
+ * gives a message for the calling thread's most recent failure.  A CUDA error
+ * inside a call is returned as KGS_ERR_CUDA and is also kept in the handle
+ * (every later call on it returns KGS_ERR_CUDA until it is destroyed).
+ */
+#ifndef KGS_H
+#define KGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define KGS_OK            0
+#define KGS_ERR_ARG      -1  /* invalid argument (dim, L, parameters, NULL pointer, where) */
+#define KGS_ERR_ODD_N    -2  /* N odd or N < 4: the periodic checkerboard needs even N */
+#define KGS_ERR_OOM      -3  /* device allocation failed */
+#define KGS_ERR_CUDA     -4  /* a CUDA call failed (also: no usable device) */
+#define KGS_ERR_STATE    -5  /* no state set yet */
+#define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out */
+#define KGS_ERR_RANGE    -7  /* size beyond what the call supports */
+
+/* memory kind of caller buffers */
+#define KGS_HOST   0
+#define KGS_DEVICE 1
+
+/* state precision (kgs_create_ex) */
+#define KGS_FP64 64  /* state and arithmetic in float64 */
+#define KGS_FP32 32  /* state and arithmetic in float32; invariants in float64 */
+
+/* options (kgs_set_option) */
+#define KGS_OPT_KERNEL   1  /* 0 auto, 1 one launch per colour pass, 2 shared-memory resident */
+#define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
+
+typedef struct kgs_solver* kgs_handle;
+
+/* Create a solver for dimension dim in {1,2,3}, N points per direction (even,
+ * >= 4), period L > 0, finite kappa1, kappa2, mu, gamma (either sign) and a
+ * finite, nonzero time step tau (negative tau runs the scheme backwards,
+ * Eq. dp-comp being symmetric).  FP64 state on the current device.
+ * Allocates 2 * N^d * 16 bytes of state plus N^d * 8 bytes of staging and a
+ * few KB of reduction scratch.  Returns NULL on error (see kgs_last_error). */
+kgs_handle kgs_create(int dim, int64_t N, double L, double kappa1, double kappa2,
+                      double mu, double gamma, double tau);
+
+/* As kgs_create, with precision KGS_FP64 or KGS_FP32 and a CUDA device index
+ * (-1 = the current device).  FP32 halves the state bytes. */
+kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kappa2,
+                         double mu, double gamma, double tau, int precision, int device);
+
+/* Copy a state in: four float64 arrays of N^d elements each (layout above),
+ * host memory (where = KGS_HOST; pinned or pageable; returns after the copy)
+ * or device memory of the handle's device (where = KGS_DEVICE; asynchronous on
+ * stream; the buffers must stay valid until the stream reaches this point).
+ * FP32 handles round each value to float32. */
+int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* U,
+                  const double* V, int where, void* stream);
+
+/* Copy the state out as four float64 arrays (FP32 state is widened exactly).
+ * Host buffers are filled when the call returns; device buffers are written
+ * asynchronously on stream. */
+int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V,
+                  int where, void* stream);
+
+/* Advance the state by nsteps >= 0 full DP-AVF2 steps of size tau (Eq. dp-comp
+ * in the checkerboard order of Algorithm 3), asynchronously on stream.  On
+ * completion the state is at a step boundary; kgs_step(a) then kgs_step(b)
+ * gives bitwise the result of kgs_step(a + b). */
+int kgs_step(kgs_handle h, int64_t nsteps, void* stream);
+
+/* Discrete invariants of the current state, computed on the device in float64
+ * with compensated final summation, returned in host memory (synchronises
+ * stream):
+ *   out[0] = E_h = h^d sum [1/2 (kappa1 |grad_h psi|^2 + kappa2 |grad_h u|^2
+ *                  + v^2 + mu^2 u^2) - gamma |psi|^2 u]   (Sec. 2, Eq. ene-origin;
+ *            grad_h the forward difference, via summation by parts)
+ *   out[1] = h^d sum of the absolute values of those five terms (a scale for
+ *            relative energy errors: E_h has no fixed sign)
+ *   out[2] = mass h^d sum |psi|^2 (the discrete norm of Sec. 2; the scheme does
+ *            not conserve it -- a diagnostic only). */
+int kgs_invariants(kgs_handle h, double* out3, void* stream);
+
+/* E_h and the mass alone (out[0] and out[2] of kgs_invariants). */
+int kgs_energy(kgs_handle h, double* E);
+int kgs_mass(kgs_handle h, double* M);
+
+/* Change the time step (finite, nonzero; either sign).  Takes effect for the
+ * next kgs_step. */
+int kgs_set_tau(kgs_handle h, double tau);
+
+/* Tuning options (KGS_OPT_*); values out of range return KGS_ERR_ARG. */
+int kgs_set_option(kgs_handle h, int option, int64_t value);
+
+/* Number of kernels this handle has launched so far (graph replays count
+ * each kernel node).  For benchmarks. */
+int64_t kgs_launch_count(kgs_handle h);
+
+/* Free every device buffer of the handle.  NULL is ignored. */
+void kgs_destroy(kgs_handle h);
+
+/* Static message for a status code. */
+const char* kgs_strerror(int status);
+
+/* Message of the calling thread's most recent error ("" if none). */
+const char* kgs_last_error(void);
+
+/* Status of the calling thread's most recent failed call (KGS_OK if none);
+ * the way to learn why kgs_create / kgs_create_ex returned NULL. */
+int kgs_last_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KGS_H */

@@ -1,0 +1,33 @@
+/*
+ * kgs_probe.h -- measurement kernels of libkgs (no counterpart in the paper).
+ *
+ * The DP-AVF2 colour passes in float64 are bound by the FP64 pipe of the B300,
+ * whose rate the measured-peaks file does not give.  This probe measures it
+ * (and the FP32 rate) the way a roofline denominator is usually taken: many
+ * independent fused multiply-add chains per thread, enough CTAs to fill every
+ * SM, timed with CUDA events on the given stream.
+ */
+#ifndef KGS_PROBE_H
+#define KGS_PROBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Run `iters` iterations of 8 independent FMA chains in every thread of a grid
+ * of 148 * blocks_per_sm CTAs x 256 threads, in float64 (precision 64) or
+ * float32 (precision 32), on the current device and `stream` (cudaStream_t as
+ * void*, NULL = legacy default).  Writes the elapsed milliseconds and the FMA
+ * rate in FMA/s (one FMA = 2 flops).  Synchronises the stream.
+ * Returns 0, -1 for a bad argument (iters < 1, blocks_per_sm < 1 or > 64,
+ * precision not 32/64, NULL outputs) or -4 if a CUDA call failed. */
+int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* stream,
+                       double* elapsed_ms, double* fma_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KGS_PROBE_H */

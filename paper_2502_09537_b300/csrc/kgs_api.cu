@@ -1,0 +1,509 @@
+// kgs_api.cu -- the C ABI of libkgs (declared and documented in include/kgs.h).
+//
+// A handle owns its device state ((P,Q) and (U,V) as vec2 arrays in the state
+// precision), a float64 staging buffer for layout conversion, and reduction
+// scratch.  kgs_step issues the fused colour passes of a checkerboard DP-AVF2
+// run (RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ; see
+// kgs_point.cuh): small grids as one shared-memory resident launch, larger
+// ones as one launch per pass, the repeated (BLACK_FUSED, RED_FUSED) pairs
+// replayed from a captured CUDA graph.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/kgs.h"
+#include "kgs_internal.h"
+
+using namespace kgs;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+thread_local int g_last_status = 0;
+
+int fail(int status, const char* fmt, ...)
+{
+    g_last_status = status;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+// Pairs of colour passes per captured graph.
+constexpr int kGraphPairs = 32;
+
+}  // namespace
+
+struct kgs_solver {
+    int dim = 0, precision = 64, device = 0;
+    int64_t N = 0, M = 0;
+    double L = 0, h = 0, kappa1 = 0, kappa2 = 0, mu = 0, gamma = 0, tau = 0;
+    void* pq = nullptr;
+    void* uv = nullptr;
+    double* stage = nullptr;
+    double* partials = nullptr;
+    double* out_dev = nullptr;
+    double* out_host = nullptr;
+    int nblocks = 0;
+    bool state_set = false;
+    int sticky = 0;  // first CUDA error seen (cudaError_t), 0 if none
+    int opt_kernel = 0, opt_graph = 1;
+    cudaStream_t last_stream = nullptr;
+    int64_t launches = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    Coef<double> cd{};
+    Coef<float> cf{};
+};
+
+namespace {
+
+// Makes h's device current for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int cuda_fail(kgs_solver* h, cudaError_t e, const char* what)
+{
+    if (h && !h->sticky) h->sticky = (int)e;
+    return fail(KGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int check_handle(kgs_solver* h)
+{
+    if (!h) return fail(KGS_ERR_ARG, "NULL handle");
+    if (h->sticky)
+        return fail(KGS_ERR_CUDA, "handle is in error state after: %s",
+                    cudaGetErrorString((cudaError_t)h->sticky));
+    return KGS_OK;
+}
+
+bool is_finite_(double x) { return std::isfinite(x); }
+
+void compute_coef(kgs_solver* h)
+{
+    const double s = h->tau / 2.0;
+    const double h2 = h->h * h->h;
+    Coef<double> c;
+    c.beta = s * h->kappa1 / (2.0 * h2);
+    c.alpha = (double)h->dim * c.beta;
+    c.g = s * h->gamma / 2.0;
+    c.B = s * h->kappa2 / h2;
+    const double A = (double)h->dim * c.B + s * h->mu * h->mu / 2.0;
+    c.E = s * h->gamma;
+    c.twoA = 2.0 * A;
+    c.As = A * s;
+    c.s = s;
+    c.hs = s / 2.0;
+    c.inv_det = 1.0 / (1.0 + A * s / 2.0);
+    h->cd = c;
+    h->cf.beta = (float)c.beta;
+    h->cf.alpha = (float)c.alpha;
+    h->cf.g = (float)c.g;
+    h->cf.B = (float)c.B;
+    h->cf.E = (float)c.E;
+    h->cf.twoA = (float)c.twoA;
+    h->cf.As = (float)c.As;
+    h->cf.s = (float)c.s;
+    h->cf.hs = (float)c.hs;
+    h->cf.inv_det = (float)c.inv_det;
+}
+
+void drop_graph(kgs_solver* h)
+{
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
+Grid grid_of(const kgs_solver* h) { return Grid{h->dim, h->N, h->M}; }
+
+bool use_smem(const kgs_solver* h)
+{
+    const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
+    if (h->opt_kernel == 1) return false;
+    if (h->opt_kernel == 2) return h->M <= cap;
+    return h->M <= cap;
+}
+
+template <typename T>
+int pass(kgs_solver* h, int mode, cudaStream_t s)
+{
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    int n = launch_pass<T>(grid_of(h), mode, (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c, s);
+    if (n < 0) return -1;
+    h->launches += n;
+    return 0;
+}
+
+template <typename T>
+int ensure_graph(kgs_solver* h)
+{
+    if (h->graph) return 0;
+    if (!h->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+    }
+    cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    for (int k = 0; k < kGraphPairs; ++k) {
+        launch_pass<T>(grid_of(h), BLACK_FUSED, (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c,
+                       h->capture_stream);
+        launch_pass<T>(grid_of(h), RED_FUSED, (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c,
+                       h->capture_stream);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    return 0;
+}
+
+template <typename T>
+int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
+{
+    if (use_smem(h)) {
+        const Coef<T>* c;
+        if constexpr (sizeof(T) == 8) c = &h->cd;
+        else c = &h->cf;
+        int n = launch_smem_run<T>(grid_of(h), (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c, nsteps, s);
+        if (n < 0) return cuda_fail(h, cudaGetLastError(), "shared-memory run launch");
+        h->launches += n;
+        return KGS_OK;
+    }
+    if (pass<T>(h, RED_BASE, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
+    int64_t pairs = nsteps - 1;
+    if (h->opt_graph && pairs >= kGraphPairs) {
+        if (ensure_graph<T>(h)) return KGS_ERR_CUDA;
+        while (pairs >= kGraphPairs) {
+            cudaError_t e = cudaGraphLaunch(h->graph, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            h->launches += 2 * kGraphPairs;
+            pairs -= kGraphPairs;
+        }
+    }
+    for (; pairs > 0; --pairs) {
+        if (pass<T>(h, BLACK_FUSED, s) || pass<T>(h, RED_FUSED, s))
+            return cuda_fail(h, cudaGetLastError(), "colour pass launch");
+    }
+    if (pass<T>(h, BLACK_FUSED, s) || pass<T>(h, RED_ADJ, s))
+        return cuda_fail(h, cudaGetLastError(), "colour pass launch");
+    return KGS_OK;
+}
+
+void free_all(kgs_solver* h)
+{
+    drop_graph(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    cudaFree(h->pq);
+    cudaFree(h->uv);
+    cudaFree(h->stage);
+    cudaFree(h->partials);
+    cudaFree(h->out_dev);
+    if (h->out_host) cudaFreeHost(h->out_host);
+}
+
+}  // namespace
+
+extern "C" {
+
+kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kappa2, double mu,
+                         double gamma, double tau, int precision, int device)
+{
+    g_last_error[0] = '\0';
+    g_last_status = KGS_OK;
+    if (dim < 1 || dim > 3) { fail(KGS_ERR_ARG, "dim must be 1, 2 or 3 (got %d)", dim); return nullptr; }
+    if (N < 4 || (N & 1)) {
+        fail(KGS_ERR_ODD_N, "N must be even and >= 4 (got %lld)", (long long)N);
+        return nullptr;
+    }
+    if (N > (int64_t)1 << 20 || (dim >= 2 && N > (int64_t)1 << 17) || (dim == 3 && N > 4096)) {
+        fail(KGS_ERR_RANGE, "N^d too large (dim %d, N %lld)", dim, (long long)N);
+        return nullptr;
+    }
+    if (!is_finite_(L) || L <= 0) { fail(KGS_ERR_ARG, "L must be finite and > 0"); return nullptr; }
+    if (!is_finite_(kappa1) || !is_finite_(kappa2) || !is_finite_(mu) || !is_finite_(gamma)) {
+        fail(KGS_ERR_ARG, "kappa1, kappa2, mu, gamma must be finite");
+        return nullptr;
+    }
+    if (!is_finite_(tau) || tau == 0.0) { fail(KGS_ERR_ARG, "tau must be finite and nonzero"); return nullptr; }
+    if (precision != KGS_FP64 && precision != KGS_FP32) {
+        fail(KGS_ERR_ARG, "precision must be KGS_FP64 or KGS_FP32 (got %d)", precision);
+        return nullptr;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        fail(KGS_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    if (device < 0) {
+        if (cudaGetDevice(&device) != cudaSuccess) { fail(KGS_ERR_CUDA, "cudaGetDevice failed"); return nullptr; }
+    }
+    if (device >= ndev) { fail(KGS_ERR_ARG, "device %d out of range (%d devices)", device, ndev); return nullptr; }
+    DeviceGuard guard(device);
+    if (!guard.ok) { fail(KGS_ERR_CUDA, "cudaSetDevice(%d) failed", device); return nullptr; }
+
+    kgs_solver* h = new (std::nothrow) kgs_solver();
+    if (!h) { fail(KGS_ERR_OOM, "host allocation failed"); return nullptr; }
+    h->dim = dim;
+    h->N = N;
+    h->M = 1;
+    for (int a = 0; a < dim; ++a) h->M *= N;
+    h->L = L;
+    h->h = L / (double)N;
+    h->kappa1 = kappa1;
+    h->kappa2 = kappa2;
+    h->mu = mu;
+    h->gamma = gamma;
+    h->tau = tau;
+    h->precision = precision;
+    h->device = device;
+    compute_coef(h);
+    const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
+    const size_t state_bytes = (size_t)h->M * elem;
+    h->nblocks = invariants_blocks(h->M);
+    cudaError_t ea = cudaMalloc(&h->pq, state_bytes);
+    if (ea == cudaSuccess) ea = cudaMalloc(&h->uv, state_bytes);
+    if (ea == cudaSuccess) ea = cudaMalloc(&h->stage, (size_t)h->M * sizeof(double));
+    if (ea == cudaSuccess) ea = cudaMalloc(&h->partials, (size_t)h->nblocks * 3 * sizeof(double));
+    if (ea == cudaSuccess) ea = cudaMalloc(&h->out_dev, 3 * sizeof(double));
+    if (ea == cudaSuccess) ea = cudaMallocHost(&h->out_host, 3 * sizeof(double));
+    if (ea != cudaSuccess) {
+        cudaGetLastError();
+        int status = (ea == cudaErrorMemoryAllocation) ? KGS_ERR_OOM : KGS_ERR_CUDA;
+        fail(status, "device allocation of %zu state bytes failed: %s", 2 * state_bytes,
+             cudaGetErrorString(ea));
+        free_all(h);
+        delete h;
+        return nullptr;
+    }
+    return h;
+}
+
+kgs_handle kgs_create(int dim, int64_t N, double L, double kappa1, double kappa2, double mu,
+                      double gamma, double tau)
+{
+    return kgs_create_ex(dim, N, L, kappa1, kappa2, mu, gamma, tau, KGS_FP64, -1);
+}
+
+int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* U, const double* V,
+                  int where, void* stream)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (!P || !Q || !U || !V) return fail(KGS_ERR_ARG, "NULL state pointer");
+    if (where != KGS_HOST && where != KGS_DEVICE) return fail(KGS_ERR_ARG, "where must be KGS_HOST or KGS_DEVICE");
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* src[4] = {P, Q, U, V};
+    for (int f = 0; f < 4; ++f) {
+        const double* d = src[f];
+        if (where == KGS_HOST) {
+            cudaError_t e = cudaMemcpyAsync(h->stage, src[f], (size_t)h->M * sizeof(double),
+                                            cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "state upload");
+            d = h->stage;
+        }
+        void* dst = (f < 2) ? h->pq : h->uv;
+        int n = (h->precision == 64)
+                    ? launch_pack<double>(h->M, (double2*)dst, f & 1, d, s)
+                    : launch_pack<float>(h->M, (float2*)dst, f & 1, d, s);
+        if (n < 0) return cuda_fail(h, cudaGetLastError(), "pack launch");
+        h->launches += n;
+    }
+    if (where == KGS_HOST) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+    h->state_set = true;
+    h->last_stream = s;
+    return KGS_OK;
+}
+
+int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int where, void* stream)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (!h->state_set) return fail(KGS_ERR_STATE, "no state set");
+    if (!P || !Q || !U || !V) return fail(KGS_ERR_ARG, "NULL state pointer");
+    if (where != KGS_HOST && where != KGS_DEVICE) return fail(KGS_ERR_ARG, "where must be KGS_HOST or KGS_DEVICE");
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* dst[4] = {P, Q, U, V};
+    for (int f = 0; f < 4; ++f) {
+        double* d = (where == KGS_HOST) ? h->stage : dst[f];
+        const void* src = (f < 2) ? h->pq : h->uv;
+        int n = (h->precision == 64)
+                    ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s)
+                    : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s);
+        if (n < 0) return cuda_fail(h, cudaGetLastError(), "unpack launch");
+        h->launches += n;
+        if (where == KGS_HOST) {
+            cudaError_t e = cudaMemcpyAsync(dst[f], h->stage, (size_t)h->M * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "state download");
+        }
+    }
+    if (where == KGS_HOST) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+    return KGS_OK;
+}
+
+int kgs_step(kgs_handle h, int64_t nsteps, void* stream)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (nsteps < 0) return fail(KGS_ERR_ARG, "nsteps must be >= 0");
+    if (!h->state_set) return fail(KGS_ERR_STATE, "no state set");
+    h->last_stream = (cudaStream_t)stream;
+    if (nsteps == 0) return KGS_OK;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+    return h->precision == 64 ? step_impl<double>(h, nsteps, (cudaStream_t)stream)
+                              : step_impl<float>(h, nsteps, (cudaStream_t)stream);
+}
+
+int kgs_invariants(kgs_handle h, double* out3, void* stream)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (!out3) return fail(KGS_ERR_ARG, "NULL output");
+    if (!h->state_set) return fail(KGS_ERR_STATE, "no state set");
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    InvParams p;
+    p.kappa1 = h->kappa1;
+    p.kappa2 = h->kappa2;
+    p.mu = h->mu;
+    p.gamma = h->gamma;
+    p.inv_h2 = 1.0 / (h->h * h->h);
+    p.hd = 1.0;
+    for (int a = 0; a < h->dim; ++a) p.hd *= h->h;
+    int n = (h->precision == 64)
+                ? launch_invariants<double>(grid_of(h), (const double2*)h->pq, (const double2*)h->uv, p,
+                                            h->partials, h->nblocks, h->out_dev, s)
+                : launch_invariants<float>(grid_of(h), (const float2*)h->pq, (const float2*)h->uv, p,
+                                           h->partials, h->nblocks, h->out_dev, s);
+    if (n < 0) return cuda_fail(h, cudaGetLastError(), "invariants launch");
+    h->launches += n;
+    cudaError_t e = cudaMemcpyAsync(h->out_host, h->out_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "invariants readback");
+    for (int k = 0; k < 3; ++k) out3[k] = h->out_host[k];
+    return KGS_OK;
+}
+
+int kgs_energy(kgs_handle h, double* E)
+{
+    if (!E) return fail(KGS_ERR_ARG, "NULL output");
+    double out[3];
+    int st = kgs_invariants(h, out, h ? (void*)h->last_stream : nullptr);
+    if (st == KGS_OK) *E = out[0];
+    return st;
+}
+
+int kgs_mass(kgs_handle h, double* M)
+{
+    if (!M) return fail(KGS_ERR_ARG, "NULL output");
+    double out[3];
+    int st = kgs_invariants(h, out, h ? (void*)h->last_stream : nullptr);
+    if (st == KGS_OK) *M = out[2];
+    return st;
+}
+
+int kgs_set_tau(kgs_handle h, double tau)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (!is_finite_(tau) || tau == 0.0) return fail(KGS_ERR_ARG, "tau must be finite and nonzero");
+    h->tau = tau;
+    compute_coef(h);
+    drop_graph(h);
+    return KGS_OK;
+}
+
+int kgs_set_option(kgs_handle h, int option, int64_t value)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    switch (option) {
+    case KGS_OPT_KERNEL:
+        if (value < 0 || value > 2) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0, 1 or 2");
+        if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))
+            return fail(KGS_ERR_RANGE, "grid too large for the shared-memory resident kernel");
+        h->opt_kernel = (int)value;
+        return KGS_OK;
+    case KGS_OPT_GRAPH:
+        if (value < 0 || value > 1) return fail(KGS_ERR_ARG, "KGS_OPT_GRAPH takes 0 or 1");
+        h->opt_graph = (int)value;
+        return KGS_OK;
+    default:
+        return fail(KGS_ERR_ARG, "unknown option %d", option);
+    }
+}
+
+int64_t kgs_launch_count(kgs_handle h) { return h ? h->launches : -1; }
+
+void kgs_destroy(kgs_handle h)
+{
+    if (!h) return;
+    {
+        DeviceGuard guard(h->device);
+        free_all(h);
+    }
+    delete h;
+}
+
+const char* kgs_strerror(int status)
+{
+    switch (status) {
+    case KGS_OK: return "ok";
+    case KGS_ERR_ARG: return "invalid argument";
+    case KGS_ERR_ODD_N: return "N must be even and >= 4";
+    case KGS_ERR_OOM: return "device out of memory";
+    case KGS_ERR_CUDA: return "CUDA error";
+    case KGS_ERR_STATE: return "no state set";
+    case KGS_ERR_TIMEOUT: return "device wait timed out";
+    case KGS_ERR_RANGE: return "size out of supported range";
+    default: return "unknown status";
+    }
+}
+
+const char* kgs_last_error(void) { return g_last_error; }
+
+int kgs_last_status(void) { return g_last_status; }
+
+}  // extern "C"

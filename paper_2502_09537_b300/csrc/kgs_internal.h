@@ -1,0 +1,50 @@
+// kgs_internal.h -- declarations shared by the .cu files of libkgs (not public).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kgs_point.cuh"
+
+namespace kgs {
+
+// Geometry of one periodic grid: N points per direction, M = N^dim points.
+struct Grid {
+    int dim;
+    int64_t N;
+    int64_t M;
+};
+
+// Largest point count the shared-memory resident kernel takes for state type T
+// (whole (P,Q) and (U,V) arrays in one CTA's shared memory).
+int64_t smem_resident_max_points(int elem_bytes);
+
+// Sweep launchers (kgs_sweep.cu).  pq/uv hold the state as vec2 (P,Q) and (U,V)
+// in natural order.  All launches go to `stream`; each returns the number of
+// kernels it launched, or -1 if a launch failed (cudaGetLastError is set).
+template <typename T>
+int launch_pass(const Grid& g, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                cudaStream_t stream);
+template <typename T>
+int launch_smem_run(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                    int64_t nsteps, cudaStream_t stream);
+
+// Layout conversion (kgs_layout.cu): one float64 field <-> one component of a vec2 array.
+template <typename T>
+int launch_pack(int64_t M, vec2_t<T>* dst, int comp, const double* src, cudaStream_t stream);
+template <typename T>
+int launch_unpack(int64_t M, double* dst, const vec2_t<T>* src, int comp, cudaStream_t stream);
+
+// Invariants (kgs_reduce.cu): E_h, its absolute-term scale, and the mass.
+struct InvParams {
+    double kappa1, kappa2, mu, gamma;
+    double inv_h2;  // 1 / h^2
+    double hd;      // h^dim
+};
+int invariants_blocks(int64_t M);
+template <typename T>
+int launch_invariants(const Grid& g, const vec2_t<T>* pq, const vec2_t<T>* uv,
+                      const InvParams& p, double* partials, int nblocks, double* out3,
+                      cudaStream_t stream);
+
+}  // namespace kgs

@@ -1,0 +1,57 @@
+// kgs_probe.cu -- FMA issue-rate probe (declared in include/kgs_probe.h).
+// No counterpart in the paper: it measures the FP64 pipe rate that bounds the
+// float64 colour passes, for the roofline denominator.
+#include "../../include/kgs_probe.h"
+
+#include <cuda_runtime.h>
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_chains(int64_t iters, T b, T c, T* sink)
+{
+    T a0 = (T)threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+    T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+    for (int64_t k = 0; k < iters; ++k) {
+        a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+    T s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (s == (T)-12345.678) sink[blockIdx.x] = s;  // keeps the chains live
+}
+
+template <typename T>
+int run(int64_t iters, int bps, cudaStream_t s, double* ms, double* rate)
+{
+    const int blocks = 148 * bps;
+    T* sink = nullptr;
+    if (cudaMalloc(&sink, blocks * sizeof(T)) != cudaSuccess) return -4;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fma_chains<T><<<blocks, 256, 0, s>>>(iters / 8 + 1, (T)0.999999, (T)1e-6, sink);  // warm-up
+    cudaEventRecord(e0, s);
+    fma_chains<T><<<blocks, 256, 0, s>>>(iters, (T)0.999999, (T)1e-6, sink);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return -4;
+    *ms = t;
+    *rate = (double)blocks * 256.0 * 8.0 * (double)iters / (t * 1e-3);
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* stream,
+                                  double* elapsed_ms, double* fma_per_s)
+{
+    if (iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 64 || !elapsed_ms || !fma_per_s) return -1;
+    if (precision == 64) return run<double>(iters, blocks_per_sm, (cudaStream_t)stream, elapsed_ms, fma_per_s);
+    if (precision == 32) return run<float>(iters, blocks_per_sm, (cudaStream_t)stream, elapsed_ms, fma_per_s);
+    return -1;
+}

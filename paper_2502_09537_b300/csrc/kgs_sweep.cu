@@ -1,0 +1,214 @@
+// kgs_sweep.cu -- checkerboard colour-pass kernels of the DP-AVF2 scheme.
+//
+// The paper's GPU ordering (Sec. 4.2, Algorithm 3) updates every point of one
+// colour concurrently, since no point has a neighbour of its own colour (N
+// even).  Here one step is two fused colour passes (see PassMode in
+// kgs_point.cuh) instead of Algorithm 3's four, and each pass computes its
+// neighbour sums once for both of the half-step updates it applies.
+//
+// Two variants, bitwise identical (same pointwise code, same neighbour order):
+//   pass_kernel       one launch per colour pass over an N^d grid in global
+//                     memory; one thread per point of the pass's colour.
+//   smem_run_kernel   a whole n-step run inside one CTA with the state resident
+//                     in shared memory (small grids: the 1D workloads).
+#include "kgs_internal.h"
+
+namespace kgs {
+
+// Linear index of the t-th point of the colour whose 0-based index sum has
+// parity `parity`, and its 2*D periodic neighbours in the order
+// (axis 0 down, axis 0 up, axis 1 down, ...).  Rows run along the last axis;
+// each row holds N/2 points of each colour.
+template <int D>
+__device__ __forceinline__ int64_t colour_point(int64_t t, int64_t N, int parity, int64_t nb[2 * D])
+{
+    const int64_t hN = N >> 1;
+    const int64_t row = t / hN;
+    const int64_t kk = t - row * hN;
+    int64_t i0 = 0, i1 = 0;
+    int rp = 0;
+    if (D == 2) {
+        i0 = row;
+        rp = (int)(i0 & 1);
+    } else if (D == 3) {
+        i0 = row / N;
+        i1 = row - i0 * N;
+        rp = (int)((i0 + i1) & 1);
+    }
+    const int64_t k = 2 * kk + ((parity - rp) & 1);
+    const int64_t i = row * N + k;
+    const int64_t km = (k == 0) ? i + (N - 1) : i - 1;
+    const int64_t kp = (k == N - 1) ? i - (N - 1) : i + 1;
+    if (D == 1) {
+        nb[0] = km;
+        nb[1] = kp;
+    } else if (D == 2) {
+        nb[0] = (i0 == 0) ? i + (N - 1) * N : i - N;
+        nb[1] = (i0 == N - 1) ? i - (N - 1) * N : i + N;
+        nb[2] = km;
+        nb[3] = kp;
+    } else {
+        const int64_t N2 = N * N;
+        nb[0] = (i0 == 0) ? i + (N - 1) * N2 : i - N2;
+        nb[1] = (i0 == N - 1) ? i - (N - 1) * N2 : i + N2;
+        nb[2] = (i1 == 0) ? i + (N - 1) * N : i - N;
+        nb[3] = (i1 == N - 1) ? i - (N - 1) * N : i + N;
+        nb[4] = km;
+        nb[5] = kp;
+    }
+    return i;
+}
+
+// Neighbour sums in the fixed order of colour_point.
+template <typename T, int D, bool GLOBAL>
+__device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t<T>* uv,
+                                               const int64_t nb[2 * D], T& SP, T& SQ, T& SU)
+{
+    const T* u = reinterpret_cast<const T*>(uv);
+    vec2_t<T> a = GLOBAL ? __ldg(&pq[nb[0]]) : pq[nb[0]];
+    T su = GLOBAL ? __ldg(&u[2 * nb[0]]) : u[2 * nb[0]];
+    T sp = a.x, sq = a.y;
+#pragma unroll
+    for (int n = 1; n < 2 * D; ++n) {
+        vec2_t<T> b = GLOBAL ? __ldg(&pq[nb[n]]) : pq[nb[n]];
+        T ub = GLOBAL ? __ldg(&u[2 * nb[n]]) : u[2 * nb[n]];
+        sp = add_(sp, b.x);
+        sq = add_(sq, b.y);
+        su = add_(su, ub);
+    }
+    SP = sp;
+    SQ = sq;
+    SU = su;
+}
+
+template <typename T, int D, int MODE, bool GLOBAL>
+__device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int64_t t, int64_t N,
+                                              int parity, const Coef<T>& c)
+{
+    int64_t nb[2 * D];
+    const int64_t i = colour_point<D>(t, N, parity, nb);
+    T SP, SQ, SU;
+    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, SP, SQ, SU);
+    vec2_t<T> a = pq[i];
+    vec2_t<T> b = uv[i];
+    update_point<T, MODE>(c, SP, SQ, SU, a.x, a.y, b.x, b.y);
+    pq[i] = a;
+    uv[i] = b;
+}
+
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(256) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N,
+                                                   int64_t half, Coef<T> c, int parity)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= half) return;
+    colour_update<T, D, MODE, true>(pq, uv, t, N, parity, c);
+}
+
+template <typename T, int D, int MODE>
+__device__ __forceinline__ void smem_pass(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, int64_t half,
+                                          int parity, const Coef<T>& c)
+{
+    for (int64_t t = threadIdx.x; t < half; t += blockDim.x)
+        colour_update<T, D, MODE, false>(pq, uv, t, N, parity, c);
+    __syncthreads();
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(1024) smem_run_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N,
+                                                        int64_t M, Coef<T> c, int64_t nsteps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec2_t<T>* spq = reinterpret_cast<vec2_t<T>*>(smem_raw);
+    vec2_t<T>* suv = spq + M;
+    for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+        spq[i] = pq[i];
+        suv[i] = uv[i];
+    }
+    __syncthreads();
+    const int64_t half = M >> 1;
+    const int red = red_parity(D), black = red ^ 1;
+    smem_pass<T, D, RED_BASE>(spq, suv, N, half, red, c);
+    for (int64_t n = 1; n < nsteps; ++n) {
+        smem_pass<T, D, BLACK_FUSED>(spq, suv, N, half, black, c);
+        smem_pass<T, D, RED_FUSED>(spq, suv, N, half, red, c);
+    }
+    smem_pass<T, D, BLACK_FUSED>(spq, suv, N, half, black, c);
+    smem_pass<T, D, RED_ADJ>(spq, suv, N, half, red, c);
+    for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+        pq[i] = spq[i];
+        uv[i] = suv[i];
+    }
+}
+
+int64_t smem_resident_max_points(int elem_bytes)
+{
+    // 227 KB of dynamic shared memory per CTA on sm_103a; 2 vec2 per point.
+    const int64_t bytes = 227 * 1024;
+    return bytes / (4 * (int64_t)elem_bytes);
+}
+
+template <typename T, int D, int MODE>
+static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                          cudaStream_t s)
+{
+    const int64_t half = g.M >> 1;
+    const int threads = 256;
+    const int64_t blocks = (half + threads - 1) / threads;
+    const int parity = (MODE == BLACK_FUSED) ? (red_parity(D) ^ 1) : red_parity(D);
+    pass_kernel<T, D, MODE><<<(unsigned)blocks, threads, 0, s>>>(pq, uv, g.N, half, c, parity);
+}
+
+template <typename T, int D>
+static void launch_pass_d(const Grid& g, int mode, vec2_t<T>* pq, vec2_t<T>* uv,
+                          const Coef<T>& c, cudaStream_t s)
+{
+    switch (mode) {
+    case RED_BASE: launch_pass_t<T, D, RED_BASE>(g, pq, uv, c, s); break;
+    case BLACK_FUSED: launch_pass_t<T, D, BLACK_FUSED>(g, pq, uv, c, s); break;
+    case RED_FUSED: launch_pass_t<T, D, RED_FUSED>(g, pq, uv, c, s); break;
+    default: launch_pass_t<T, D, RED_ADJ>(g, pq, uv, c, s); break;
+    }
+}
+
+template <typename T>
+int launch_pass(const Grid& g, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                cudaStream_t stream)
+{
+    if (g.dim == 1) launch_pass_d<T, 1>(g, mode, pq, uv, c, stream);
+    else if (g.dim == 2) launch_pass_d<T, 2>(g, mode, pq, uv, c, stream);
+    else launch_pass_d<T, 3>(g, mode, pq, uv, c, stream);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <typename T, int D>
+static int launch_smem_d(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                         int64_t nsteps, cudaStream_t s)
+{
+    const size_t bytes = (size_t)g.M * 2 * sizeof(vec2_t<T>);
+    if (cudaFuncSetAttribute(smem_run_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+        return -1;
+    int threads = (int)((g.M / 2 + 31) / 32 * 32);
+    if (threads > 1024) threads = 1024;
+    if (threads < 32) threads = 32;
+    smem_run_kernel<T, D><<<1, threads, bytes, s>>>(pq, uv, g.N, g.M, c, nsteps);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <typename T>
+int launch_smem_run(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c, int64_t nsteps,
+                    cudaStream_t stream)
+{
+    if (g.M > smem_resident_max_points((int)sizeof(T))) return -1;
+    if (g.dim == 1) return launch_smem_d<T, 1>(g, pq, uv, c, nsteps, stream);
+    if (g.dim == 2) return launch_smem_d<T, 2>(g, pq, uv, c, nsteps, stream);
+    return launch_smem_d<T, 3>(g, pq, uv, c, nsteps, stream);
+}
+
+template int launch_pass<double>(const Grid&, int, double2*, double2*, const Coef<double>&, cudaStream_t);
+template int launch_pass<float>(const Grid&, int, float2*, float2*, const Coef<float>&, cudaStream_t);
+template int launch_smem_run<double>(const Grid&, double2*, double2*, const Coef<double>&, int64_t, cudaStream_t);
+template int launch_smem_run<float>(const Grid&, float2*, float2*, const Coef<float>&, int64_t, cudaStream_t);
+
+}  // namespace kgs

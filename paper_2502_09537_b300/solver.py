@@ -1,0 +1,205 @@
+"""Thin ctypes binding of libkgs (the C ABI declared in ``include/kgs.h``).
+
+Argument marshalling only: every step of the DP-AVF2 path runs in the CUDA
+kernels of ``libkgs.so``.  There is no CPU fallback: if the library is missing
+or no GPU is present the calls raise.
+
+State arguments are four float64 arrays (P, Q, U, V) of shape (N,)*d in C
+order: numpy arrays (host) or CUDA torch tensors (device; passed by pointer).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkgs.so")
+
+KGS_OK = 0
+KGS_HOST = 0
+KGS_DEVICE = 1
+KGS_FP64 = 64
+KGS_FP32 = 32
+KGS_OPT_KERNEL = 1
+KGS_OPT_GRAPH = 2
+
+# Every function the header declares, with its ctypes signature.
+_c_int64 = ctypes.c_int64
+_c_dbl = ctypes.c_double
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "kgs_create": (_vp, [ctypes.c_int, _c_int64] + [_c_dbl] * 6),
+    "kgs_create_ex": (_vp, [ctypes.c_int, _c_int64] + [_c_dbl] * 6 + [ctypes.c_int, ctypes.c_int]),
+    "kgs_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "kgs_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "kgs_step": (ctypes.c_int, [_vp, _c_int64, _vp]),
+    "kgs_invariants": (ctypes.c_int, [_vp, _dp, _vp]),
+    "kgs_energy": (ctypes.c_int, [_vp, _dp]),
+    "kgs_mass": (ctypes.c_int, [_vp, _dp]),
+    "kgs_set_tau": (ctypes.c_int, [_vp, _c_dbl]),
+    "kgs_set_option": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64]),
+    "kgs_launch_count": (_c_int64, [_vp]),
+    "kgs_destroy": (None, [_vp]),
+    "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "kgs_last_error": (ctypes.c_char_p, []),
+    "kgs_last_status": (ctypes.c_int, []),
+    # include/kgs_probe.h
+    "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
+}
+
+_lib = None
+
+
+class KGSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libkgs status {status}: {msg}")
+        self.status = status
+
+
+def load_library():
+    """Load libkgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libkgs.so not built at {LIB_PATH}; run "
+                              "`python -m paper_2502_09537_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load_library().kgs_last_error().decode()
+
+
+def _check(status: int):
+    if status != KGS_OK:
+        raise KGSError(status, last_error())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _as_buffers(arrays: Sequence, N: int, dim: int):
+    """Return (where, pointers, keepalive) for four state arrays."""
+    shape = (N,) * dim
+    if all(isinstance(a, np.ndarray) for a in arrays):
+        out = []
+        for a in arrays:
+            if a.shape != shape or a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError(f"host state arrays must be C-contiguous float64 {shape}")
+            out.append(a)
+        return KGS_HOST, [a.ctypes.data for a in out], out
+    import torch
+    out = []
+    for a in arrays:
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64
+                and tuple(a.shape) == shape and a.is_contiguous()):
+            raise ValueError(f"device state tensors must be contiguous CUDA float64 {shape}")
+        out.append(a)
+    return KGS_DEVICE, [a.data_ptr() for a in out], out
+
+
+class Solver:
+    """One periodic KGS problem advanced by the DP-AVF2 checkerboard scheme."""
+
+    def __init__(self, dim: int, N: int, L: float, kappa1: float, kappa2: float, mu: float,
+                 gamma: float, tau: float, precision: int = KGS_FP64, device: int = -1):
+        lib = load_library()
+        self._lib = lib
+        h = lib.kgs_create_ex(dim, N, L, kappa1, kappa2, mu, gamma, tau, precision, device)
+        if not h:
+            raise KGSError(lib.kgs_last_status(), last_error())
+        self._h = ctypes.c_void_p(h)
+        self.dim, self.N, self.L, self.precision = dim, N, L, precision
+
+    @classmethod
+    def from_problem(cls, prob, precision: int = KGS_FP64, device: int = -1) -> "Solver":
+        return cls(prob.dim, prob.N, prob.L, prob.kappa1, prob.kappa2, prob.mu, prob.gamma,
+                   prob.tau, precision, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kgs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # state ---------------------------------------------------------------
+    def set_state(self, P, Q, U, V, stream=None):
+        where, ptrs, _keep = _as_buffers((P, Q, U, V), self.N, self.dim)
+        _check(self._lib.kgs_set_state(self._h, *ptrs, where, _stream_ptr(stream)))
+
+    def get_state(self, out=None, stream=None):
+        """Return (P, Q, U, V).  With out=None, new numpy arrays; otherwise fills
+        the four given numpy arrays or CUDA tensors."""
+        if out is None:
+            out = tuple(np.empty((self.N,) * self.dim) for _ in range(4))
+        where, ptrs, _keep = _as_buffers(out, self.N, self.dim)
+        _check(self._lib.kgs_get_state(self._h, *ptrs, where, _stream_ptr(stream)))
+        return tuple(out)
+
+    # stepping ------------------------------------------------------------
+    def step(self, nsteps: int, stream=None):
+        _check(self._lib.kgs_step(self._h, int(nsteps), _stream_ptr(stream)))
+
+    def set_tau(self, tau: float):
+        _check(self._lib.kgs_set_tau(self._h, float(tau)))
+
+    def set_option(self, option: int, value: int):
+        _check(self._lib.kgs_set_option(self._h, int(option), int(value)))
+
+    # diagnostics ---------------------------------------------------------
+    def invariants(self, stream=None):
+        """(E_h, S_E, mass) in float64."""
+        out = (ctypes.c_double * 3)()
+        _check(self._lib.kgs_invariants(self._h, ctypes.cast(out, _dp), _stream_ptr(stream)))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def energy(self) -> float:
+        e = ctypes.c_double()
+        _check(self._lib.kgs_energy(self._h, ctypes.byref(e)))
+        return e.value
+
+    def mass(self) -> float:
+        m = ctypes.c_double()
+        _check(self._lib.kgs_mass(self._h, ctypes.byref(m)))
+        return m.value
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.kgs_launch_count(self._h))
+
+
+def probe_fma_rate(precision: int = 64, iters: int = 4096, blocks_per_sm: int = 8, stream=None):
+    """Measured FMA rate of the FP64 (or FP32) pipe in FMA/s (include/kgs_probe.h)."""
+    lib = load_library()
+    ms, rate = ctypes.c_double(), ctypes.c_double()
+    st = lib.kgs_probe_fma_rate(precision, iters, blocks_per_sm, _stream_ptr(stream),
+                                ctypes.byref(ms), ctypes.byref(rate))
+    if st != 0:
+        raise KGSError(st, "FMA probe failed")
+    return rate.value, ms.value

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar for float64 state: per field, max-norm difference / max-norm of the
+oracle's field <= 1e-12 after the run's steps.  Both sides solve the same
+equations in the same order (checkerboard, increment form); they differ only
+in rounding (the kernels use fused multiply-adds and a reciprocal, the oracle
+separate roundings and a complex division), and the scheme amplifies a
+one-ulp difference by at most a few hundred over 1000 steps (measured on the
+oracle), so differences stay near 1e-14.
+
+Sizes: full configurations where the oracle finishes in seconds; for the
+full 2048^2 and 512^3 grids, the first steps against the oracle's OpenMP twin
+(bitwise equal to the serial oracle) plus energy conservation over the whole
+run, a property that holds at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2502_09537_b300 import inputs  # noqa: E402
+from paper_2502_09537_b300.inputs import Problem, random_state  # noqa: E402
+from paper_2502_09537_b300.solver import (KGS_FP32, KGS_FP64, KGS_OPT_GRAPH,  # noqa: E402
+                                          KGS_OPT_KERNEL, Solver)
+
+FP64_BAR = 1e-12
+
+
+def copy_state(st):
+    return tuple(np.array(a, dtype=np.float64, copy=True) for a in st)
+
+
+def run_gpu(prob, st, nsteps, precision=KGS_FP64, kernel=0, graph=1, splits=None):
+    with Solver.from_problem(prob, precision) as s:
+        s.set_option(KGS_OPT_KERNEL, kernel)
+        s.set_option(KGS_OPT_GRAPH, graph)
+        s.set_state(*copy_state(st))
+        for n in (splits or [nsteps]):
+            s.step(n)
+        return s.get_state()
+
+
+def run_oracle(orc, prob, st, nsteps, threads=0):
+    out = copy_state(st)
+    if threads:
+        orc.steps_checkerboard_omp(prob, *out, nsteps, threads)
+    else:
+        orc.steps_checkerboard(prob, *out, nsteps)
+    return out
+
+
+def rel_err(a, b):
+    return max(np.abs(x - y).max() / max(np.abs(y).max(), 1e-300) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("case", [
+    "soliton1d_N512_2000",      # the 1D configuration, full size (shared-memory kernel)
+    "gauss2d_N250_300",         # ragged: N^2/2 = 31250 points per colour
+    "gauss2d_N256_tau_h2_2.62", # the 2D configuration's tau/h^2, 1000 steps
+    "gauss3d_N42_200",          # 3D, ragged
+    "exp3_3d_N32_100",          # negative kappa1 (Sec. 5.2 parameters)
+])
+def test_fp64_matches_oracle(orc, case):
+    if case == "soliton1d_N512_2000":
+        w = inputs.soliton_1d(512, 2000)
+        prob, st, n = w.prob, w.state, w.nsteps
+    elif case == "gauss2d_N250_300":
+        w = inputs.gauss_2d(250, 300)
+        prob, st, n = w.prob, w.state, w.nsteps
+    elif case == "gauss2d_N256_tau_h2_2.62":
+        w = inputs.gauss_2d(256, 1000)
+        prob = w.prob._replace(tau=2.62 * w.prob.h ** 2)
+        st, n = w.state, 1000
+    elif case == "gauss3d_N42_200":
+        w = inputs.gauss_3d(42, 200)
+        prob, st, n = w.prob, w.state, w.nsteps
+    else:
+        w = inputs.paper_exp3_ellipsoids_3d(32, 0.01, 100)
+        prob, st, n = w.prob, w.state, w.nsteps
+    gpu = run_gpu(prob, st, n)
+    ref = run_oracle(orc, prob, st, n, threads=0 if prob.points * n < 3e7 else 8)
+    err = rel_err(gpu, ref)
+    print(f"{case}: max-norm relative difference {err:.3e}")
+    assert err <= FP64_BAR
+
+
+@pytest.mark.parametrize("dim,N", [(1, 4), (1, 6), (2, 4), (2, 6), (3, 4), (3, 6), (1, 10), (2, 12)])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_tiny_grids_both_kernels(orc, dim, N, kernel):
+    prob = Problem(dim, N, 3.0 + N / 7, 1.1, 0.9, 1.2, 0.8, 0.02)
+    st = random_state(prob, 100 + N + dim, 0.7)
+    gpu = run_gpu(prob, st, 50, kernel=kernel)
+    ref = run_oracle(orc, prob, st, 50)
+    assert rel_err(gpu, ref) <= FP64_BAR
+
+
+def test_kernel_variants_and_graphs_are_bitwise_equal():
+    prob = Problem(2, 64, 10.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 3, 0.5)
+    a = run_gpu(prob, st, 100, kernel=1, graph=1)
+    b = run_gpu(prob, st, 100, kernel=1, graph=0)
+    c = run_gpu(prob, st, 100, kernel=2)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_split_steps_are_bitwise_equal(kernel):
+    """kgs_step(a); kgs_step(b) == kgs_step(a+b), across graph boundaries too."""
+    prob = Problem(2, 48, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 4, 0.5)
+    whole = run_gpu(prob, st, 100, kernel=kernel)
+    parts = run_gpu(prob, st, 100, kernel=kernel, splits=[1, 40, 27, 32])
+    for x, y in zip(whole, parts):
+        assert np.array_equal(x, y)
+
+
+def test_device_pointer_path_matches_host_path():
+    prob = Problem(3, 16, 6.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 8, 0.5)
+    host = run_gpu(prob, st, 20)
+    dev = [torch.from_numpy(a.copy()).cuda() for a in st]
+    out = [torch.empty_like(d) for d in dev]
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with Solver.from_problem(prob) as s:
+        s.set_state(*dev, stream=stream)
+        s.step(20, stream=stream)
+        s.get_state(out, stream=stream)
+        stream.synchronize()
+    for x, y in zip(host, out):
+        assert np.array_equal(x, y.cpu().numpy())
+
+
+@pytest.mark.parametrize("dim,N", [(1, 64), (2, 24), (3, 10)])
+def test_invariants_match_oracle(orc, dim, N):
+    prob = Problem(dim, N, 7.0, 1.3, 0.7, 0.9, 1.1, 0.01)
+    st = random_state(prob, 50 + dim, 0.8)
+    with Solver.from_problem(prob) as s:
+        s.set_state(*copy_state(st))
+        E, S, M = s.invariants()
+    Eo, So, Mo = orc.invariants(prob, *st)
+    assert abs(E - Eo) <= 1e-13 * So
+    assert abs(S - So) <= 1e-13 * So
+    assert abs(M - Mo) <= 1e-13 * Mo
+
+
+def test_energy_conserved_on_gpu_over_1e4_steps():
+    prob = Problem(2, 32, 2 * math.pi, 1.0, 1.0, 1.0, 1.0, 0.05)
+    st = random_state(prob, 12, 0.6)
+    with Solver.from_problem(prob) as s:
+        s.set_option(KGS_OPT_KERNEL, 1)
+        s.set_state(*copy_state(st))
+        E0, S0, _ = s.invariants()
+        worst = 0.0
+        for _ in range(10):
+            s.step(1000)
+            E, S, _ = s.invariants()
+            worst = max(worst, abs(E - E0) / max(S0, S))
+    print(f"GPU energy drift over 1e4 steps: {worst:.2e}")
+    assert worst <= 1e-12
+
+
+def test_full_size_2d_first_steps_and_energy(orc):
+    """2048^2 grid of the 2D configuration: 3 steps against the oracle's OpenMP
+    twin, then energy over all 1000 steps, logged every 100."""
+    w = inputs.gauss_2d(2048, 1000)
+    ref = run_oracle(orc, w.prob, w.state, 3, threads=orc.max_threads())
+    with Solver.from_problem(w.prob) as s:
+        s.set_state(*copy_state(w.state))
+        s.step(3)
+        assert rel_err(s.get_state(), ref) <= FP64_BAR
+        s.set_state(*copy_state(w.state))
+        E0, S0, _ = s.invariants()
+        worst = 0.0
+        for _ in range(10):
+            s.step(100)
+            E, S, _ = s.invariants()
+            worst = max(worst, abs(E - E0) / max(S0, S))
+    print(f"2D 2048^2 energy drift over 1000 steps: {worst:.2e}")
+    assert worst <= 1e-12
+
+
+def test_fp32_state_close_to_fp64_oracle(orc):
+    """Float32 state and arithmetic: not bit-comparable; its max-norm error
+    against the FP64 oracle and its energy drift are reported and bounded by
+    what float32 rounding (6e-8 per operation) allows over the run."""
+    w = inputs.soliton_1d(512, 2000)
+    ref = run_oracle(orc, w.prob, w.state, w.nsteps)
+    with Solver.from_problem(w.prob, KGS_FP32) as s:
+        s.set_state(*copy_state(w.state))
+        E0, S0, _ = s.invariants()
+        s.step(w.nsteps)
+        E1, S1, _ = s.invariants()
+        got = s.get_state()
+    err = rel_err(got, ref)
+    drift = abs(E1 - E0) / max(S0, S1)
+    print(f"fp32 1D soliton: max-norm rel error {err:.2e}, energy drift {drift:.2e}")
+    assert err < 1e-3
+    assert drift < 1e-4
