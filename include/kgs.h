@@ -141,6 +141,32 @@ const char* kgs_last_error(void);
  * the way to learn why kgs_create / kgs_create_ex returned NULL. */
 int kgs_last_status(void);
 
+/* ---- allocation-free invariants (no counterpart in the paper) ----------
+ * The same three values as kgs_invariants (E_h, S_E, mass), for callers that
+ * cannot allocate device memory where they need them: code whose GPU memory
+ * is all owned by its own arena or budget, host threads that cannot afford
+ * the implicit synchronisation of cudaMalloc, or callers that cannot create a
+ * kgs handle (handle creation allocates).  No handle is involved and the call
+ * allocates nothing: it reads the caller's state and writes the caller's
+ * output, and keeps its reduction scratch in one fixed 192 KB array inside
+ * libkgs that every GPU which loads the library holds until the process exits.
+ *
+ * P, Q, U, V: float64 device arrays of N^dim points in the layout above, on
+ * the current device.  out3: float64 device array of 3, written
+ * asynchronously on stream (cudaStream_t as void*, NULL = legacy default).
+ * The grid may hold at most KGS_NOALLOC_MAX_POINTS points; larger grids are
+ * rejected with KGS_ERR_RANGE before any work.  Invalid arguments return
+ * KGS_ERR_ARG, CUDA failures KGS_ERR_CUDA (see kgs_last_error).
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one scratch array: calls that can
+ * run at the same time on the GPU (e.g. unordered streams) race and may return
+ * wrong values; order them on one stream or with events. */
+#define KGS_NOALLOC_MAX_POINTS 33554432  /* 8192 partial triples x 4096 points each */
+int kgs_invariants_noalloc(int dim, int64_t N, double L, double kappa1, double kappa2,
+                           double mu, double gamma, const double* P, const double* Q,
+                           const double* U, const double* V, double* out3, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -231,6 +231,8 @@ void free_all(kgs_solver* h)
 
 }  // namespace
 
+int kgs::report_error(int status, const char* msg) { return fail(status, "%s", msg); }
+
 extern "C" {
 
 kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kappa2, double mu,

@@ -47,4 +47,8 @@ int launch_invariants(const Grid& g, const vec2_t<T>* pq, const vec2_t<T>* uv,
                       const InvParams& p, double* partials, int nblocks, double* out3,
                       cudaStream_t stream);
 
+// Record status and message as the calling thread's last error (what
+// kgs_last_status / kgs_last_error return); returns status.
+int report_error(int status, const char* msg);
+
 }  // namespace kgs

@@ -47,6 +47,8 @@ SIGNATURES = {
     "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kgs_last_error": (ctypes.c_char_p, []),
     "kgs_last_status": (ctypes.c_int, []),
+    "kgs_invariants_noalloc": (ctypes.c_int, [ctypes.c_int, _c_int64] + [_c_dbl] * 5
+                               + [_vp, _vp, _vp, _vp, _vp, _vp]),
     # include/kgs_probe.h
     "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
 }
