@@ -37,11 +37,23 @@ ENERGY_EVERY = 100
 
 def flops_per_point_update(dim: int) -> float:
     """Algorithmic flops of one point-update (one point, one full DP-AVF2 step)
-    in the fused colour-pass formulation (kgs_point.cuh), FMA = 2, add/mul/
-    reciprocal = 1: neighbour sums 3(2d-1); black pass 2 x (r 2 + 1/(1+r^2) 3
-    + Psi 15) + t 6 + 2 x (U,V) 10 = 66; red pass t 6 + (U,V) 10 + r 2 +
-    1/(1+r^2) 3 + 2 x Psi 15 + t 6 + (U,V) 10 = 67; mean over the colours."""
-    return 3 * (2 * dim - 1) + 66.5
+    as the colour passes compute it (kgs_point.cuh), FMA = 2, add/mul/
+    reciprocal estimate = 1: neighbour sums 3(2d-1); beta S 2; Psi prepare 10
+    (r 2, 2r 1, 1 + r^2 2, reciprocal 1 + 3 FMA), Psi apply 12, (U,V) source 6,
+    one (U,V) step 7.  Black pass: 2 + 10 + 12 + 6 + 2x7 + 10 + 12 = 66;
+    red pass: 2 + 6 + 7 + 10 + 2x12 + 6 + 7 = 62; a point-update is the mean."""
+    return 3 * (2 * dim - 1) + (66 + 62) / 2
+
+
+# DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
+# ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
+# the kernels as they are now; None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("2d", "fp64"): 134.36e6 + 74.77e6}
+
+# FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
+# sm__sass_thread_inst_executed_op_dfma_pred_on), 148 SMs, 2032 MHz maximum SM
+# clock -> 2 x 2 x 148 x 2.032e9 = 1.203e12 flop/s.
+FP64_PEAK_TFLOPS = 2 * 2 * 148 * 2.032e9 / 1e12
 
 
 def bytes_per_point_update(elem: int) -> int:
@@ -290,10 +302,12 @@ def main():
         fma_rate, _ = probe_fma_rate(64, 2048, 8, stream)
         flops_per_launch = prob.points / 2 * flops_per_point_update(prob.dim)
         achieved = flops_per_launch / (pass_ms * 1e-3) / 1e12
-        peak = 2 * fma_rate / 1e12
+        peak = FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FP64 FMA rate x 2 (kgs_probe_fma_rate, same run)",
+                "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+                "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
+                "probe_tflops": 2 * fma_rate / 1e12,
                 "flops_per_point_update": flops_per_point_update(prob.dim),
                 "hbm_frac": bytes_per_point_update(elem) * prob.points / 2 / (pass_ms * 1e-3)
                 / 1e9 / peaks.get("hbm_gbs", 6400.0)}
@@ -302,7 +316,8 @@ def main():
         achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
 
     line = {

@@ -26,6 +26,16 @@ extern "C" {
 int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* stream,
                        double* elapsed_ms, double* fma_per_s);
 
+/* Accuracy of the float64 reciprocal the colour passes use for 1/(1 + r^2):
+ * evaluates it on n arguments d = 1 + r^2, r spread over [-rmax, rmax] by a
+ * fixed hash of the sample index, against CUDA's IEEE division 1.0/d, on the
+ * current device and stream (synchronised).  Writes the largest difference in
+ * units in the last place and the number of samples that differ at all.
+ * Returns 0, -1 for a bad argument (n < 1, rmax not finite or <= 0, NULL
+ * outputs) or -4 if a CUDA call failed. */
+int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
+                      int64_t* n_differ);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,31 +97,36 @@ bool is_finite_(double x) { return std::isfinite(x); }
 
 void compute_coef(kgs_solver* h)
 {
+    // Half step s = tau/2; coefficients of Eq. scheme1 written for dimension d
+    // (kgs_point.cuh).  Everything in FP64; FP32 handles round the results.
     const double s = h->tau / 2.0;
     const double h2 = h->h * h->h;
+    const double d = (double)h->dim;
+    const double beta = s * h->kappa1 / (2.0 * h2);
+    const double B = s * h->kappa2 / h2;
+    const double A = d * B + s * h->mu * h->mu / 2.0;
+    const double E = s * h->gamma;
+    const double inv_det = 1.0 / (1.0 + A * s / 2.0);
     Coef<double> c;
-    c.beta = s * h->kappa1 / (2.0 * h2);
-    c.alpha = (double)h->dim * c.beta;
+    c.alpha = d * beta;
     c.g = s * h->gamma / 2.0;
-    c.B = s * h->kappa2 / h2;
-    const double A = (double)h->dim * c.B + s * h->mu * h->mu / 2.0;
-    c.E = s * h->gamma;
-    c.twoA = 2.0 * A;
-    c.As = A * s;
+    c.beta = beta;
+    c.Bp = B * inv_det;
+    c.Ep = E * inv_det;
+    c.twoAp = 2.0 * A * inv_det;
     c.s = s;
     c.hs = s / 2.0;
-    c.inv_det = 1.0 / (1.0 + A * s / 2.0);
     h->cd = c;
-    h->cf.beta = (float)c.beta;
-    h->cf.alpha = (float)c.alpha;
-    h->cf.g = (float)c.g;
-    h->cf.B = (float)c.B;
-    h->cf.E = (float)c.E;
-    h->cf.twoA = (float)c.twoA;
-    h->cf.As = (float)c.As;
-    h->cf.s = (float)c.s;
-    h->cf.hs = (float)c.hs;
-    h->cf.inv_det = (float)c.inv_det;
+    Coef<float> f;
+    f.alpha = (float)c.alpha;
+    f.g = (float)c.g;
+    f.beta = (float)c.beta;
+    f.Bp = (float)c.Bp;
+    f.Ep = (float)c.Ep;
+    f.twoAp = (float)c.twoAp;
+    f.s = (float)c.s;
+    f.hs = (float)c.hs;
+    h->cf = f;
 }
 
 void drop_graph(kgs_solver* h)

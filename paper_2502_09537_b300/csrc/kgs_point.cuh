@@ -20,8 +20,13 @@
 // (U,V) update (last two equations of Eq. scheme1) in increment form:
 //   (1 + A s/2) dV = B SU + E rho - 2 A U - A s V,   dU = s V + (s/2) dV,
 // with SU the sum of the neighbours' U and rho = |Psi|^2 at the point.
-// Increment form keeps each update's rounding proportional to the increment;
-// the direct form drifts E_h by about one ulp per step.
+// Increment form keeps each update's rounding proportional to the increment
+// (constants that are not exact multiply only the increment); the direct form
+// drifts E_h by about one ulp per step.
+//
+// The colour passes are bound by the FP64 pipe, so the code below is arranged
+// to minimise FP64 instructions per point (about 47 in 2D) without giving up
+// the exact structure described below.
 //
 // Which U* and rho each half uses (Eqs. scheme1, dp-avf-kj-adj):
 //   base Phi_s    : Psi with U^n, then (U,V) with |Psi^{n+1}|^2
@@ -38,11 +43,14 @@ template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 template <typename T> using vec2_t = typename Vec2<T>::type;
 
-// Half-step coefficients in the state precision (computed on the host in FP64).
+// Half-step coefficients in the state precision (computed on the host in FP64,
+// see kgs_api.cu).  Names as in the header comment; primes mark constants
+// pre-multiplied by inv_det = 1 / (1 + A s/2).
 template <typename T> struct Coef {
-    T beta, alpha, g;
-    T B, E, twoA, As;
-    T s, hs, inv_det;
+    T alpha, g;        // r = alpha - g U
+    T beta;            // Psi neighbour weight
+    T Bp, Ep, twoAp;   // B', E', 2A'
+    T s, hs;           // s = tau/2, s/2
 };
 
 // ------------------------------------------------- rounded arithmetic --
@@ -52,47 +60,82 @@ __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
+// Reciprocal of a >= 1 in float64: the hardware estimate (rcp.approx.ftz.f64,
+// about 20 correct bits from the high word) refined by one step of the
+// cubically convergent Newton-Raphson iteration for 1/a,
+//   e = 1 - a y,   y <- y + y (e + e^2)
+// (J.-M. Muller et al., Handbook of Floating-Point Arithmetic, ch. on Newton-
+// Raphson division), whose error after the step is about e^3 ~ 2^-60 before
+// the final rounding: within one ulp of the IEEE quotient (kgs_probe.h
+// measures it against CUDA's division).  Three FP64 FMAs instead of the
+// longer correctly rounded sequence; here the reciprocal only scales an
+// increment, so one ulp in it is far below one ulp of the state.
+__device__ __forceinline__ double rcp_(double a)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    const double e = __fma_rn(-a, y, 1.0);
+    return __fma_rn(y, __fma_rn(e, e, e), y);
+}
 __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 
 // --------------------------------------------------------- pointwise --
-template <typename T> __device__ __forceinline__ T r_of(const Coef<T>& c, T u)
+// Structure that must hold exactly in floating point, not only algebraically:
+// the Psi update is a Cayley transform, (i - r) Psi' = (i + r) Psi - beta S,
+// which keeps |Psi| when S = 0.  Its increment 2 r Psi - beta S is formed
+// with 2r = r + r (exact) and the same r as the denominator, so rounding only
+// enters through per-point roundings of unbiased sign; scaling 2r by a
+// rounded constant instead would break |i + r| = |i - r| by that constant's
+// rounding at every update and drift E_h steadily.  Likewise the (U,V) update
+// is written as the implicit midpoint rule it is, U' = U + (s/2)(V + V'), so
+// that s enters through s/2 alone.
+
+// The Psi update for one value of r, prepared once and applied once or twice
+// (the red pass applies the adjoint and the next base update with the same U,
+// hence the same r).
+template <typename T> struct PsiPrep {
+    T r, r2, w;  // r, 2r, 1/(1 + r^2)
+};
+
+template <typename T> __device__ __forceinline__ PsiPrep<T> psi_prep(const Coef<T>& c, T u)
 {
-    return fma_(-c.g, u, c.alpha);
+    PsiPrep<T> pp;
+    pp.r = fma_(-c.g, u, c.alpha);
+    pp.r2 = add_(pp.r, pp.r);
+    pp.w = rcp_(fma_(pp.r, pp.r, T(1)));
+    return pp;
 }
 
-template <typename T> __device__ __forceinline__ T inv_of(T r)
-{
-    return rcp_(fma_(r, r, T(1)));
-}
-
-// Psi <- Psi + dPsi for a given r and inv = 1 / (1 + r^2).
+// dPsi = (2r Psi - beta S) / (i - r):
+//   N = 2r Psi - bS,  dP = (N_im - r N_re) w,  dQ = -(N_re + r N_im) w,
+// with (bSP, bSQ) = beta S computed once per point and pass.
 template <typename T>
-__device__ __forceinline__ void psi_step(const Coef<T>& c, T r, T inv, T SP, T SQ, T& P, T& Q)
+__device__ __forceinline__ void psi_apply(const PsiPrep<T>& pp, T bSP, T bSQ, T& P, T& Q)
 {
-    T r2 = add_(r, r);
-    T nre = fma_(r2, P, -mul_(c.beta, SP));
-    T nim = fma_(r2, Q, -mul_(c.beta, SQ));
-    T dP = mul_(fma_(-r, nre, nim), inv);
-    T dQ = -mul_(fma_(r, nim, nre), inv);
-    P = add_(P, dP);
-    Q = add_(Q, dQ);
+    const T nre = fma_(pp.r2, P, -bSP);
+    const T nim = fma_(pp.r2, Q, -bSQ);
+    const T tP = fma_(-pp.r, nre, nim);
+    const T tQ = fma_(pp.r, nim, nre);
+    P = fma_(tP, pp.w, P);
+    Q = fma_(-tQ, pp.w, Q);
 }
 
-// t = B SU + E rho: the part of the (U,V) right side fixed by the neighbours and |Psi|^2.
+// t' = (B SU + E |Psi|^2) / (1 + A s/2): the part of the (U,V) right side
+// fixed by the neighbours and the point's |Psi|^2.
 template <typename T> __device__ __forceinline__ T uv_src(const Coef<T>& c, T SU, T P, T Q)
 {
-    T rho = fma_(P, P, mul_(Q, Q));
-    return fma_(c.B, SU, mul_(c.E, rho));
+    const T rho = fma_(P, P, mul_(Q, Q));
+    return fma_(c.Bp, SU, mul_(c.Ep, rho));
 }
 
+// One (U,V) update, the implicit midpoint rule of the last two equations of
+// Eq. scheme1:  a = U + (s/2) V,  dV = t' - 2A' a,  V' = V + dV,  U' = a + (s/2) V'.
 template <typename T> __device__ __forceinline__ void uv_step(const Coef<T>& c, T t, T& U, T& V)
 {
-    T rhs = fma_(-c.twoA, U, fma_(-c.As, V, t));
-    T dV = mul_(rhs, c.inv_det);
-    T dU = fma_(c.hs, dV, mul_(c.s, V));
-    U = add_(U, dU);
+    const T a = fma_(c.hs, V, U);
+    const T dV = fma_(-c.twoAp, a, t);
     V = add_(V, dV);
+    U = fma_(c.hs, V, a);
 }
 
 // The four kinds of colour pass of a checkerboard DP-AVF2 run
@@ -101,6 +144,8 @@ template <typename T> __device__ __forceinline__ void uv_step(const Coef<T>& c, 
 // red-adjoint of step n and red-base of step n+1 see the same black
 // neighbours, so they fuse too.  A run of n steps is
 //   RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ.
+// RED_FUSED computes exactly RED_ADJ followed by RED_BASE, so a run split
+// into several calls gives bitwise the same state.
 enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3 };
 
 // Update one point of the pass's colour in registers.  SP, SQ, SU are the
@@ -109,29 +154,27 @@ template <typename T, int MODE>
 __device__ __forceinline__ void update_point(const Coef<T>& c, T SP, T SQ, T SU,
                                              T& P, T& Q, T& U, T& V)
 {
+    const T bSP = mul_(c.beta, SP), bSQ = mul_(c.beta, SQ);
     if (MODE == RED_BASE) {
-        T r = r_of(c, U);
-        psi_step(c, r, inv_of(r), SP, SQ, P, Q);
-        uv_step(c, uv_src(c, SU, P, Q), U, V);
+        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
+        uv_step(c, uv_src(c, SU, P, Q), U, V);      // base (U,V) with |Psi^{n+1}|^2
     } else if (MODE == BLACK_FUSED) {
-        T r = r_of(c, U);
-        psi_step(c, r, inv_of(r), SP, SQ, P, Q);   // base Psi with U^n
-        T t = uv_src(c, SU, P, Q);                 // |Psi^{n+1}|^2 = the adjoint's |Psi^n|^2
-        uv_step(c, t, U, V);                       // base (U,V)
-        uv_step(c, t, U, V);                       // adjoint (U,V)
-        T r2 = r_of(c, U);
-        psi_step(c, r2, inv_of(r2), SP, SQ, P, Q); // adjoint Psi with U^{n+1}
+        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
+        // base and adjoint (U,V): both use |Psi^{n+1}|^2 of the base half (the
+        // adjoint's |Psi^n|^2) and the same neighbours
+        const T t = uv_src(c, SU, P, Q);
+        uv_step(c, t, U, V);
+        uv_step(c, t, U, V);
+        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);  // adjoint Psi with U^{n+1}
     } else if (MODE == RED_FUSED) {
-        uv_step(c, uv_src(c, SU, P, Q), U, V);     // adjoint (U,V) with |Psi^n|^2
-        T r = r_of(c, U);
-        T inv = inv_of(r);
-        psi_step(c, r, inv, SP, SQ, P, Q);         // adjoint Psi with U^{n+1}
-        psi_step(c, r, inv, SP, SQ, P, Q);         // next step's base Psi: same U, same r
-        uv_step(c, uv_src(c, SU, P, Q), U, V);     // base (U,V)
+        uv_step(c, uv_src(c, SU, P, Q), U, V);      // adjoint (U,V) with |Psi^n|^2
+        const PsiPrep<T> pp = psi_prep(c, U);
+        psi_apply(pp, bSP, bSQ, P, Q);              // adjoint Psi with U^{n+1}
+        psi_apply(pp, bSP, bSQ, P, Q);              // next base Psi: same U, same r
+        uv_step(c, uv_src(c, SU, P, Q), U, V);      // next base (U,V)
     } else {  // RED_ADJ
         uv_step(c, uv_src(c, SU, P, Q), U, V);
-        T r = r_of(c, U);
-        psi_step(c, r, inv_of(r), SP, SQ, P, Q);
+        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);
     }
 }
 

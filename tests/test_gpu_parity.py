@@ -163,7 +163,10 @@ def test_energy_conserved_on_gpu_over_1e4_steps():
             E, S, _ = s.invariants()
             worst = max(worst, abs(E - E0) / max(S0, S))
     print(f"GPU energy drift over 1e4 steps: {worst:.2e}")
-    assert worst <= 1e-12
+    # Round-off alone gives ~1e-14 here; a rounded constant that breaks the
+    # exact structure of an update (e.g. 2r scaled by a rounded 2/beta) drifts
+    # steadily to ~2e-13, which this bar catches.
+    assert worst <= 1e-13
 
 
 def test_full_size_2d_first_steps_and_energy(orc):
@@ -186,6 +189,28 @@ def test_full_size_2d_first_steps_and_energy(orc):
     assert worst <= 1e-12
 
 
+def test_full_size_3d_first_step_and_energy(orc):
+    """512^3 grid of the 3D configuration (4.3 GB of float64 state): one step
+    against the oracle's OpenMP twin, then energy over all 200 steps."""
+    w = inputs.gauss_3d(512, 200)
+    ref = run_oracle(orc, w.prob, w.state, 1, threads=orc.max_threads())
+    with Solver.from_problem(w.prob) as s:
+        s.set_state(*w.state)
+        s.step(1)
+        got = s.get_state()
+        assert rel_err(got, ref) <= FP64_BAR
+        del got, ref
+        s.set_state(*w.state)
+        E0, S0, _ = s.invariants()
+        worst = 0.0
+        for _ in range(4):
+            s.step(50)
+            E, S, _ = s.invariants()
+            worst = max(worst, abs(E - E0) / max(S0, S))
+    print(f"3D 512^3 energy drift over 200 steps: {worst:.2e}")
+    assert worst <= 1e-12
+
+
 def test_fp32_state_close_to_fp64_oracle(orc):
     """Float32 state and arithmetic: not bit-comparable; its max-norm error
     against the FP64 oracle and its energy drift are reported and bounded by
@@ -203,3 +228,13 @@ def test_fp32_state_close_to_fp64_oracle(orc):
     print(f"fp32 1D soliton: max-norm rel error {err:.2e}, energy drift {drift:.2e}")
     assert err < 1e-3
     assert drift < 1e-4
+
+
+@pytest.mark.parametrize("rmax", [1.0, 100.0, 1e6])
+def test_reciprocal_within_one_ulp_of_ieee_division(rmax):
+    """The colour passes' float64 reciprocal (hardware estimate + one cubic
+    Newton-Raphson step) against CUDA's IEEE division on 16M arguments."""
+    from paper_2502_09537_b300.solver import probe_rcp_ulp
+    worst, differ = probe_rcp_ulp(1 << 24, rmax)
+    print(f"rcp rmax={rmax}: max {worst} ulp, {differ} of {1 << 24} differ")
+    assert worst <= 1
