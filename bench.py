@@ -188,9 +188,11 @@ def run_reference(args):
     }))
 
 
-def solve(s, stream, init, nsteps, per_chunk_events=None):
+def solve(s, stream, init, nsteps, per_chunk_events=None, step_launches=None):
     """One benchmark step: load the initial state, nsteps DP-AVF2 steps with the
-    energy evaluated every ENERGY_EVERY steps.  Returns the invariants seen."""
+    energy evaluated every ENERGY_EVERY steps.  Returns the invariants seen.
+    With per_chunk_events, CUDA events bracket each kgs_step call on the stream
+    and step_launches[0] accumulates the kernels those calls launched."""
     s.set_state(*init, stream=stream)
     seen = [s.invariants(stream=stream)]
     done = 0
@@ -198,9 +200,11 @@ def solve(s, stream, init, nsteps, per_chunk_events=None):
         n = min(ENERGY_EVERY, nsteps - done)
         if per_chunk_events is not None:
             a, b = per_chunk_events.pop(0)
+            l0 = s.launch_count
             a.record(stream)
             s.step(n, stream=stream)
             b.record(stream)
+            step_launches[0] += s.launch_count - l0
         else:
             s.step(n, stream=stream)
         done += n
@@ -217,6 +221,8 @@ def main():
     ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
+    ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -245,6 +251,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     nchunks = (work.nsteps + ENERGY_EVERY - 1) // ENERGY_EVERY
     s = Solver.from_problem(prob, precision)
+    from paper_2502_09537_b300.solver import KGS_OPT_PPT, KGS_OPT_THREADS
+    if args.threads:
+        s.set_option(KGS_OPT_THREADS, args.threads)
+    if args.ppt:
+        s.set_option(KGS_OPT_PPT, args.ppt)
     torch.cuda.synchronize()
 
     with torch.cuda.stream(stream):
@@ -254,6 +265,7 @@ def main():
         if dist:
             dist.barrier()
         iter_ms, kern_ms = [], []
+        step_launches = [0]
         launches0 = s.launch_count
         drift = 0.0
         with ClockSampler(local) as clk:
@@ -264,7 +276,8 @@ def main():
                 kev = list(ev)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                seen = solve(s, stream, init_dev, work.nsteps, per_chunk_events=kev)
+                seen = solve(s, stream, init_dev, work.nsteps, per_chunk_events=kev,
+                             step_launches=step_launches)
                 e1.record(stream)
                 stream.synchronize()
                 iter_ms.append(e0.elapsed_time(e1))
@@ -294,13 +307,15 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_value = world * pts_per_step * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
 
-    # roofline of the dominant kernel: the fused colour pass
-    passes_per_chunk = 2 * ENERGY_EVERY + 1
-    pass_ms = sum(kern_ms) / (args.steps * nchunks * passes_per_chunk)
+    # roofline of the dominant kernel (the colour-pass / tile kernel that runs
+    # inside kgs_step): algorithmic work per launch / average launch duration,
+    # both over the timed region
+    pass_ms = sum(kern_ms) / step_launches[0]
+    upd_per_launch = prob.points * work.nsteps * args.steps / step_launches[0]
     peaks = measured_peaks()
     if precision == KGS_FP64:
         fma_rate, _ = probe_fma_rate(64, 2048, 8, stream)
-        flops_per_launch = prob.points / 2 * flops_per_point_update(prob.dim)
+        flops_per_launch = upd_per_launch * flops_per_point_update(prob.dim)
         achieved = flops_per_launch / (pass_ms * 1e-3) / 1e12
         peak = FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -309,10 +324,10 @@ def main():
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
                 "probe_tflops": 2 * fma_rate / 1e12,
                 "flops_per_point_update": flops_per_point_update(prob.dim),
-                "hbm_frac": bytes_per_point_update(elem) * prob.points / 2 / (pass_ms * 1e-3)
+                "hbm_frac": bytes_per_point_update(elem) * upd_per_launch / (pass_ms * 1e-3)
                 / 1e9 / peaks.get("hbm_gbs", 6400.0)}
     else:
-        bytes_per_launch = prob.points / 2 * bytes_per_point_update(elem)
+        bytes_per_launch = upd_per_launch * bytes_per_point_update(elem)
         achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -326,6 +341,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
+                   "threads": args.threads or 256, "ppt": args.ppt or 1,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",
@@ -336,7 +352,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "energy_drift": drift,
-        "pass_ms": pass_ms,
+        "kernel_ms_per_launch": pass_ms,
+        "kernel_launches_per_solve": step_launches[0] / args.steps,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(work)

@@ -62,8 +62,18 @@ extern "C" {
 #define KGS_FP32 32  /* state and arithmetic in float32; invariants in float64 */
 
 /* options (kgs_set_option) */
-#define KGS_OPT_KERNEL   1  /* 0 auto, 1 one launch per colour pass, 2 shared-memory resident */
+#define KGS_OPT_KERNEL   1  /* 0 auto, 1 one launch per colour pass, 2 shared-memory resident,
+                               3 temporally blocked tiles (dim 2, 3; allocates a second state
+                               buffer of the same size on first use) */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
+#define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
+#define KGS_OPT_PPT      4  /* points of one colour per thread in those kernels: 1 only (2 was
+                               measured no faster: the FP64 pipe, not latency, binds) */
+#define KGS_OPT_TILE_T1      5  /* tile kernel: tile extent along axis 1 (3D) */
+#define KGS_OPT_TILE_T2      6  /* tile kernel: tile extent along the last axis (even) */
+#define KGS_OPT_TILE_LX      7  /* tile kernel: axis-0 planes per CTA */
+#define KGS_OPT_TILE_PASSES  8  /* tile kernel: colour passes per launch (= halo width), 1..8 */
+#define KGS_OPT_TILE_THREADS 9  /* tile kernel: threads per CTA (64, 128, 256, 512, 1024) */
 
 typedef struct kgs_solver* kgs_handle;
 
@@ -121,7 +131,8 @@ int kgs_mass(kgs_handle h, double* M);
  * next kgs_step. */
 int kgs_set_tau(kgs_handle h, double tau);
 
-/* Tuning options (KGS_OPT_*); values out of range return KGS_ERR_ARG. */
+/* Tuning options (KGS_OPT_*); values out of range return KGS_ERR_ARG.  None
+ * changes results: every kernel variant computes bitwise the same state. */
 int kgs_set_option(kgs_handle h, int option, int64_t value);
 
 /* Number of kernels this handle has launched so far (graph replays count

@@ -42,8 +42,9 @@ struct kgs_solver {
     int dim = 0, precision = 64, device = 0;
     int64_t N = 0, M = 0;
     double L = 0, h = 0, kappa1 = 0, kappa2 = 0, mu = 0, gamma = 0, tau = 0;
-    void* pq = nullptr;
-    void* uv = nullptr;
+    void* pqb[2] = {nullptr, nullptr};  // state buffers; [cur] holds the state
+    void* uvb[2] = {nullptr, nullptr};  // ([1 - cur] is the tile kernel's output)
+    int cur = 0;
     double* stage = nullptr;
     double* partials = nullptr;
     double* out_dev = nullptr;
@@ -51,11 +52,14 @@ struct kgs_solver {
     int nblocks = 0;
     bool state_set = false;
     int sticky = 0;  // first CUDA error seen (cudaError_t), 0 if none
-    int opt_kernel = 0, opt_graph = 1;
+    int opt_kernel = 0, opt_graph = 1, opt_threads = 256;
+    TileParams tile{};
+    bool tile_set = false;  // tile parameters chosen by the caller
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    int graph_buf = -1;  // state buffer the graph was captured on
     Coef<double> cd{};
     Coef<float> cf{};
 };
@@ -137,14 +141,60 @@ void drop_graph(kgs_solver* h)
     }
 }
 
-Grid grid_of(const kgs_solver* h) { return Grid{h->dim, h->N, h->M}; }
+Grid grid_of(const kgs_solver* h)
+{
+    Grid g{h->dim, h->N, h->M};
+    g.threads = h->opt_threads;
+    return g;
+}
 
-bool use_smem(const kgs_solver* h)
+enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3 };
+
+// Default tile shape per dimension and precision (measured on B300; the batch
+// autotuner can override it per handle).
+TileParams default_tile(int dim, int precision)
+{
+    TileParams t;
+    if (dim == 2) {
+        t.T1 = 1; t.T2 = 256; t.LX = 64; t.H = t.P = 8; t.threads = 512;
+    } else if (precision == 32) {
+        t.T1 = 32; t.T2 = 32; t.LX = 64; t.H = t.P = 3; t.threads = 512;
+    } else {
+        t.T1 = 16; t.T2 = 16; t.LX = 64; t.H = t.P = 2; t.threads = 512;
+    }
+    return t;
+}
+
+int kernel_choice(const kgs_solver* h)
 {
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
-    if (h->opt_kernel == 1) return false;
-    if (h->opt_kernel == 2) return h->M <= cap;
-    return h->M <= cap;
+    if (h->opt_kernel == K_PASS || h->opt_kernel == K_SMEM || h->opt_kernel == K_TILE)
+        return h->opt_kernel;
+    if (h->M <= cap) return K_SMEM;
+    // Measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass beats the
+    // temporally blocked tiles in both precisions (FP32: 8.6e10 vs 6.2e10 /
+    // 9.8e10 vs 3.4e10 point-updates/s; FP64: 1.0e10 vs 6.1e9), so the tile
+    // kernel is chosen only on request (KGS_OPT_KERNEL = 3).
+    return K_PASS;
+}
+
+int ensure_tile_buffers(kgs_solver* h)
+{
+    if (h->pqb[1]) return 0;
+    const size_t elem = h->precision == 64 ? sizeof(double2) : sizeof(float2);
+    const size_t bytes = (size_t)h->M * elem;
+    cudaError_t e = cudaMalloc(&h->pqb[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->uvb[1], bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->pqb[1]);
+        h->pqb[1] = nullptr;
+        h->uvb[1] = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA,
+                    "second state buffer for the tile kernel (%zu bytes): %s", 2 * bytes,
+                    cudaGetErrorString(e));
+    }
+    return 0;
 }
 
 template <typename T>
@@ -153,7 +203,8 @@ int pass(kgs_solver* h, int mode, cudaStream_t s)
     const Coef<T>* c;
     if constexpr (sizeof(T) == 8) c = &h->cd;
     else c = &h->cf;
-    int n = launch_pass<T>(grid_of(h), mode, (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c, s);
+    int n = launch_pass<T>(grid_of(h), mode, (vec2_t<T>*)h->pqb[h->cur], (vec2_t<T>*)h->uvb[h->cur],
+                           *c, s);
     if (n < 0) return -1;
     h->launches += n;
     return 0;
@@ -162,7 +213,8 @@ int pass(kgs_solver* h, int mode, cudaStream_t s)
 template <typename T>
 int ensure_graph(kgs_solver* h)
 {
-    if (h->graph) return 0;
+    if (h->graph && h->graph_buf == h->cur) return 0;
+    drop_graph(h);
     if (!h->capture_stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
@@ -173,10 +225,10 @@ int ensure_graph(kgs_solver* h)
     if constexpr (sizeof(T) == 8) c = &h->cd;
     else c = &h->cf;
     for (int k = 0; k < kGraphPairs; ++k) {
-        launch_pass<T>(grid_of(h), BLACK_FUSED, (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c,
-                       h->capture_stream);
-        launch_pass<T>(grid_of(h), RED_FUSED, (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c,
-                       h->capture_stream);
+        launch_pass<T>(grid_of(h), BLACK_FUSED, (vec2_t<T>*)h->pqb[h->cur],
+                       (vec2_t<T>*)h->uvb[h->cur], *c, h->capture_stream);
+        launch_pass<T>(grid_of(h), RED_FUSED, (vec2_t<T>*)h->pqb[h->cur],
+                       (vec2_t<T>*)h->uvb[h->cur], *c, h->capture_stream);
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->capture_stream, &graph);
@@ -187,19 +239,47 @@ int ensure_graph(kgs_solver* h)
         h->graph = nullptr;
         return cuda_fail(h, e, "cudaGraphInstantiate");
     }
+    h->graph_buf = h->cur;
     return 0;
 }
 
 template <typename T>
 int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 {
-    if (use_smem(h)) {
-        const Coef<T>* c;
-        if constexpr (sizeof(T) == 8) c = &h->cd;
-        else c = &h->cf;
-        int n = launch_smem_run<T>(grid_of(h), (vec2_t<T>*)h->pq, (vec2_t<T>*)h->uv, *c, nsteps, s);
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    const int kc = kernel_choice(h);
+    if (kc == K_SMEM) {
+        int n = launch_smem_run<T>(grid_of(h), (vec2_t<T>*)h->pqb[h->cur], (vec2_t<T>*)h->uvb[h->cur],
+                                   *c, nsteps, s);
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "shared-memory run launch");
         h->launches += n;
+        return KGS_OK;
+    }
+    if (kc == K_TILE) {
+        int st = ensure_tile_buffers(h);
+        if (st) return st;
+        TileParams tp = h->tile_set ? h->tile : default_tile(h->dim, h->precision);
+        const int64_t passes = 2 * nsteps + 1;
+        const int per = tp.H;
+        for (int64_t g0 = 0; g0 < passes; g0 += per) {
+            tp.g0 = g0;
+            tp.nsteps = nsteps;
+            tp.P = (int)((passes - g0) < per ? (passes - g0) : per);
+            const int o = h->cur ^ 1;
+            int n = launch_tile<T>(grid_of(h), tp, (const vec2_t<T>*)h->pqb[h->cur],
+                                   (const vec2_t<T>*)h->uvb[h->cur], (vec2_t<T>*)h->pqb[o],
+                                   (vec2_t<T>*)h->uvb[o], *c, s);
+            if (n < 0) {
+                cudaError_t e = cudaGetLastError();
+                if (e == cudaSuccess)
+                    return fail(KGS_ERR_ARG, "tile parameters not usable for this grid");
+                return cuda_fail(h, e, "tile kernel launch");
+            }
+            h->launches += n;
+            h->cur = o;
+        }
         return KGS_OK;
     }
     if (pass<T>(h, RED_BASE, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
@@ -226,8 +306,10 @@ void free_all(kgs_solver* h)
 {
     drop_graph(h);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
-    cudaFree(h->pq);
-    cudaFree(h->uv);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->pqb[b]);
+        cudaFree(h->uvb[b]);
+    }
     cudaFree(h->stage);
     cudaFree(h->partials);
     cudaFree(h->out_dev);
@@ -250,7 +332,8 @@ kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kap
         fail(KGS_ERR_ODD_N, "N must be even and >= 4 (got %lld)", (long long)N);
         return nullptr;
     }
-    if (N > (int64_t)1 << 20 || (dim >= 2 && N > (int64_t)1 << 17) || (dim == 3 && N > 4096)) {
+    // 1D: one row; 2D: rows are launch-grid y indices (<= 65535); 3D: 4096^3 points
+    if (N > (int64_t)1 << 30 || (dim == 2 && N > 65534) || (dim == 3 && N > 4096)) {
         fail(KGS_ERR_RANGE, "N^d too large (dim %d, N %lld)", dim, (long long)N);
         return nullptr;
     }
@@ -297,8 +380,8 @@ kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kap
     const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
     const size_t state_bytes = (size_t)h->M * elem;
     h->nblocks = invariants_blocks(h->M);
-    cudaError_t ea = cudaMalloc(&h->pq, state_bytes);
-    if (ea == cudaSuccess) ea = cudaMalloc(&h->uv, state_bytes);
+    cudaError_t ea = cudaMalloc(&h->pqb[0], state_bytes);
+    if (ea == cudaSuccess) ea = cudaMalloc(&h->uvb[0], state_bytes);
     if (ea == cudaSuccess) ea = cudaMalloc(&h->stage, (size_t)h->M * sizeof(double));
     if (ea == cudaSuccess) ea = cudaMalloc(&h->partials, (size_t)h->nblocks * 3 * sizeof(double));
     if (ea == cudaSuccess) ea = cudaMalloc(&h->out_dev, 3 * sizeof(double));
@@ -340,7 +423,7 @@ int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* 
             if (e != cudaSuccess) return cuda_fail(h, e, "state upload");
             d = h->stage;
         }
-        void* dst = (f < 2) ? h->pq : h->uv;
+        void* dst = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
                     ? launch_pack<double>(h->M, (double2*)dst, f & 1, d, s)
                     : launch_pack<float>(h->M, (float2*)dst, f & 1, d, s);
@@ -369,7 +452,7 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int 
     double* dst[4] = {P, Q, U, V};
     for (int f = 0; f < 4; ++f) {
         double* d = (where == KGS_HOST) ? h->stage : dst[f];
-        const void* src = (f < 2) ? h->pq : h->uv;
+        const void* src = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
                     ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s)
                     : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s);
@@ -420,10 +503,12 @@ int kgs_invariants(kgs_handle h, double* out3, void* stream)
     p.hd = 1.0;
     for (int a = 0; a < h->dim; ++a) p.hd *= h->h;
     int n = (h->precision == 64)
-                ? launch_invariants<double>(grid_of(h), (const double2*)h->pq, (const double2*)h->uv, p,
-                                            h->partials, h->nblocks, h->out_dev, s)
-                : launch_invariants<float>(grid_of(h), (const float2*)h->pq, (const float2*)h->uv, p,
-                                           h->partials, h->nblocks, h->out_dev, s);
+                ? launch_invariants<double>(grid_of(h), (const double2*)h->pqb[h->cur],
+                                            (const double2*)h->uvb[h->cur], p, h->partials,
+                                            h->nblocks, h->out_dev, s)
+                : launch_invariants<float>(grid_of(h), (const float2*)h->pqb[h->cur],
+                                           (const float2*)h->uvb[h->cur], p, h->partials,
+                                           h->nblocks, h->out_dev, s);
     if (n < 0) return cuda_fail(h, cudaGetLastError(), "invariants launch");
     h->launches += n;
     cudaError_t e = cudaMemcpyAsync(h->out_host, h->out_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -468,14 +553,54 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     if (st) return st;
     switch (option) {
     case KGS_OPT_KERNEL:
-        if (value < 0 || value > 2) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 3");
         if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))
             return fail(KGS_ERR_RANGE, "grid too large for the shared-memory resident kernel");
+        if (value == 3 && h->dim < 2)
+            return fail(KGS_ERR_ARG, "the tile kernel needs dim 2 or 3");
         h->opt_kernel = (int)value;
         return KGS_OK;
+    case KGS_OPT_TILE_T1:
+    case KGS_OPT_TILE_T2:
+    case KGS_OPT_TILE_LX:
+    case KGS_OPT_TILE_PASSES:
+    case KGS_OPT_TILE_THREADS: {
+        if (!h->tile_set) {
+            h->tile = default_tile(h->dim, h->precision);
+            h->tile_set = true;
+        }
+        TileParams t = h->tile;
+        const int v = (int)value;
+        if (value < 1 || value > 4096) return fail(KGS_ERR_ARG, "tile option out of range");
+        if (option == KGS_OPT_TILE_T1) t.T1 = v;
+        else if (option == KGS_OPT_TILE_T2) t.T2 = v;
+        else if (option == KGS_OPT_TILE_LX) t.LX = v;
+        else if (option == KGS_OPT_TILE_PASSES) t.H = t.P = v;
+        else {
+            if (v != 64 && v != 128 && v != 256 && v != 512 && v != 1024)
+                return fail(KGS_ERR_ARG, "tile threads take 64, 128, 256, 512 or 1024");
+            t.threads = v;
+        }
+        if (t.H > 8 || t.T2 < 2 || (t.T2 & 1) || (h->dim == 3 && t.T1 < 2))
+            return fail(KGS_ERR_ARG, "tile shape out of range");
+        if (tile_smem_bytes(h->dim, h->precision == 64 ? 8 : 4, t) > 227 * 1024)
+            return fail(KGS_ERR_RANGE, "tile shape needs more than 227 KB of shared memory");
+        h->tile = t;
+        return KGS_OK;
+    }
     case KGS_OPT_GRAPH:
         if (value < 0 || value > 1) return fail(KGS_ERR_ARG, "KGS_OPT_GRAPH takes 0 or 1");
         h->opt_graph = (int)value;
+        return KGS_OK;
+    case KGS_OPT_THREADS:
+        if (value != 128 && value != 256 && value != 512)
+            return fail(KGS_ERR_ARG, "KGS_OPT_THREADS takes 128, 256 or 512");
+        h->opt_threads = (int)value;
+        drop_graph(h);
+        return KGS_OK;
+    case KGS_OPT_PPT:
+        if (value != 1) return fail(KGS_ERR_ARG, "KGS_OPT_PPT takes 1 (more points per thread "
+                                                   "measured no faster on B300)");
         return KGS_OK;
     default:
         return fail(KGS_ERR_ARG, "unknown option %d", option);

@@ -13,6 +13,7 @@ struct Grid {
     int dim;
     int64_t N;
     int64_t M;
+    int threads = 256;  // CTA size of the colour-pass kernels (128, 256 or 512)
 };
 
 // Largest point count the shared-memory resident kernel takes for state type T
@@ -28,6 +29,23 @@ int launch_pass(const Grid& g, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const Coe
 template <typename T>
 int launch_smem_run(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
                     int64_t nsteps, cudaStream_t stream);
+
+// Temporally blocked colour passes (kgs_tile.cu): passes g0 .. g0+P-1 of an
+// nsteps-step run in one launch, reading (pq, uv) and writing (pq_out, uv_out).
+struct TileParams {
+    int64_t N = 0;        // set by the launcher
+    int T1 = 32, T2 = 32; // tile extent along axis 1 and the last axis (2D: T2 only)
+    int LX = 64;          // axis-0 planes per CTA
+    int H = 4;            // halo width = largest pass count per launch
+    int P = 4;            // passes in this launch (<= H)
+    int threads = 256;
+    int64_t g0 = 0;       // run index of the launch's first pass
+    int64_t nsteps = 0;   // length of the run (its passes are 0 .. 2 nsteps)
+};
+int64_t tile_smem_bytes(int dim, int elem_bytes, const TileParams& tp);
+template <typename T>
+int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<T>* uv,
+                vec2_t<T>* pq_out, vec2_t<T>* uv_out, const Coef<T>& c, cudaStream_t stream);
 
 // Layout conversion (kgs_layout.cu): one float64 field <-> one component of a vec2 array.
 template <typename T>

@@ -9,6 +9,7 @@
 // Two variants, bitwise identical (same pointwise code, same neighbour order):
 //   pass_kernel       one launch per colour pass over an N^d grid in global
 //                     memory; one thread per point of the pass's colour.
+//   (kgs_tile.cu)     several passes per launch on shared-memory tiles.
 //   smem_run_kernel   a whole n-step run inside one CTA with the state resident
 //                     in shared memory (small grids: the 1D workloads).
 #include "kgs_internal.h"
@@ -96,13 +97,66 @@ __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int6
     uv[i] = b;
 }
 
-template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(256) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N,
-                                                   int64_t half, Coef<T> c, int parity)
+// One launch per colour pass.  The launch grid carries the row coordinates
+// (blockIdx.y = axis D-2, blockIdx.z = axis 0 for D = 3), so a thread finds its
+// point without divisions; blockIdx.x * blockDim.x + threadIdx.x runs over the
+// N/2 points of the pass's colour in the row.  32-bit indices when N^d < 2^31.
+template <typename T, int D, int MODE, typename I>
+__global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c,
+                                                   int parity)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= half) return;
-    colour_update<T, D, MODE, true>(pq, uv, t, N, parity, c);
+    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * kk >= N) return;
+    const I n = N;
+    int i0 = 0, i1 = 0, rp = 0;
+    I row = 0;
+    if (D == 2) {
+        i0 = blockIdx.y;
+        rp = i0 & 1;
+        row = i0;
+    } else if (D == 3) {
+        i0 = blockIdx.z;
+        i1 = blockIdx.y;
+        rp = (i0 + i1) & 1;
+        row = (I)i0 * n + i1;
+    }
+    const int k = 2 * kk + ((parity - rp) & 1);
+    const I i = row * n + k;
+    I nb[2 * D];
+    const I km = (k == 0) ? i + (n - 1) : i - 1;
+    const I kp = (k == N - 1) ? i - (n - 1) : i + 1;
+    if (D == 1) {
+        nb[0] = km;
+        nb[1] = kp;
+    } else if (D == 2) {
+        nb[0] = (i0 == 0) ? i + (n - 1) * n : i - n;
+        nb[1] = (i0 == N - 1) ? i - (n - 1) * n : i + n;
+        nb[2] = km;
+        nb[3] = kp;
+    } else {
+        const I n2 = n * n;
+        nb[0] = (i0 == 0) ? i + (n - 1) * n2 : i - n2;
+        nb[1] = (i0 == N - 1) ? i - (n - 1) * n2 : i + n2;
+        nb[2] = (i1 == 0) ? i + (n - 1) * n : i - n;
+        nb[3] = (i1 == N - 1) ? i - (n - 1) * n : i + n;
+        nb[4] = km;
+        nb[5] = kp;
+    }
+    const T* u = reinterpret_cast<const T*>(uv);
+    vec2_t<T> a0 = __ldg(&pq[nb[0]]);
+    T sp = a0.x, sq = a0.y, su = __ldg(&u[2 * nb[0]]);
+#pragma unroll
+    for (int m = 1; m < 2 * D; ++m) {
+        const vec2_t<T> b = __ldg(&pq[nb[m]]);
+        sp = add_(sp, b.x);
+        sq = add_(sq, b.y);
+        su = add_(su, __ldg(&u[2 * nb[m]]));
+    }
+    vec2_t<T> a = pq[i];
+    vec2_t<T> b = uv[i];
+    update_point<T, MODE>(c, sp, sq, su, a.x, a.y, b.x, b.y);
+    pq[i] = a;
+    uv[i] = b;
 }
 
 template <typename T, int D, int MODE>
@@ -152,11 +206,16 @@ template <typename T, int D, int MODE>
 static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
                           cudaStream_t s)
 {
-    const int64_t half = g.M >> 1;
-    const int threads = 256;
-    const int64_t blocks = (half + threads - 1) / threads;
+    const int hN = (int)(g.N >> 1);
+    int threads = g.threads > 0 ? g.threads : 256;
+    if (threads > hN) threads = (hN + 31) / 32 * 32;  // short rows: no idle warps
+    dim3 grid((unsigned)((hN + threads - 1) / threads), D >= 2 ? (unsigned)g.N : 1u,
+              D == 3 ? (unsigned)g.N : 1u);
     const int parity = (MODE == BLACK_FUSED) ? (red_parity(D) ^ 1) : red_parity(D);
-    pass_kernel<T, D, MODE><<<(unsigned)blocks, threads, 0, s>>>(pq, uv, g.N, half, c, parity);
+    if (g.M < ((int64_t)1 << 31))
+        pass_kernel<T, D, MODE, int32_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity);
+    else
+        pass_kernel<T, D, MODE, int64_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity);
 }
 
 template <typename T, int D>

@@ -25,6 +25,13 @@ KGS_FP64 = 64
 KGS_FP32 = 32
 KGS_OPT_KERNEL = 1
 KGS_OPT_GRAPH = 2
+KGS_OPT_THREADS = 3
+KGS_OPT_PPT = 4
+KGS_OPT_TILE_T1 = 5
+KGS_OPT_TILE_T2 = 6
+KGS_OPT_TILE_LX = 7
+KGS_OPT_TILE_PASSES = 8
+KGS_OPT_TILE_THREADS = 9
 
 # Every function the header declares, with its ctypes signature.
 _c_int64 = ctypes.c_int64

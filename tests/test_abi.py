@@ -53,7 +53,8 @@ def test_library_is_built_for_sm103a(lib):
     ((4, 16, 1.0, 1, 1, 1, 1, 0.1), -1),
     ((2, 15, 1.0, 1, 1, 1, 1, 0.1), -2),          # odd N
     ((2, 2, 1.0, 1, 1, 1, 1, 0.1), -2),           # N < 4
-    ((1, 1 << 22, 1.0, 1, 1, 1, 1, 0.1), -7),     # too large
+    ((1, (1 << 30) + 2, 1.0, 1, 1, 1, 1, 0.1), -7),  # too large
+    ((2, 65536, 1.0, 1, 1, 1, 1, 0.1), -7),
     ((3, 8192, 1.0, 1, 1, 1, 1, 0.1), -7),
     ((2, 16, 0.0, 1, 1, 1, 1, 0.1), -1),          # L
     ((2, 16, -1.0, 1, 1, 1, 1, 0.1), -1),

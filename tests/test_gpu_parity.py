@@ -109,6 +109,26 @@ def test_kernel_variants_and_graphs_are_bitwise_equal():
         assert np.array_equal(x, y) and np.array_equal(x, z)
 
 
+@pytest.mark.parametrize("dim,N", [(2, 66), (3, 18), (1, 2050)])
+@pytest.mark.parametrize("threads,ppt", [(128, 1), (512, 1)])
+def test_launch_shapes_are_bitwise_equal(dim, N, threads, ppt):
+    """CTA size and points per thread change only the launch, not the bits
+    (ragged tails included: N^d/2 is not a multiple of the CTA's points)."""
+    from paper_2502_09537_b300.solver import KGS_OPT_PPT, KGS_OPT_THREADS
+    prob = Problem(dim, N, 9.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 30 + dim, 0.5)
+    ref = run_gpu(prob, st, 40, kernel=1)
+    with Solver.from_problem(prob) as s:
+        s.set_option(KGS_OPT_KERNEL, 1)
+        s.set_option(KGS_OPT_THREADS, threads)
+        s.set_option(KGS_OPT_PPT, ppt)
+        s.set_state(*copy_state(st))
+        s.step(40)
+        got = s.get_state()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_split_steps_are_bitwise_equal(kernel):
     """kgs_step(a); kgs_step(b) == kgs_step(a+b), across graph boundaries too."""
@@ -238,3 +258,62 @@ def test_reciprocal_within_one_ulp_of_ieee_division(rmax):
     worst, differ = probe_rcp_ulp(1 << 24, rmax)
     print(f"rcp rmax={rmax}: max {worst} ulp, {differ} of {1 << 24} differ")
     assert worst <= 1
+
+
+TILE_CASES = [
+    # dim, N, T1, T2, LX, passes, threads
+    (2, 64, 1, 32, 16, 4, 128),
+    (2, 66, 1, 20, 7, 3, 64),       # ragged tiles and axis-0 ranges
+    (2, 6, 1, 16, 4, 2, 64),        # tile wider than the grid
+    (2, 130, 1, 256, 64, 8, 128),   # default 2D shape, ragged
+    (3, 18, 8, 8, 5, 2, 128),
+    (3, 20, 6, 10, 7, 3, 256),      # ragged in every axis
+    (3, 4, 8, 8, 8, 2, 64),         # tiles larger than the grid
+    (3, 34, 32, 32, 16, 3, 512),    # default 3D FP32 shape
+    (2, 40, 1, 16, 9, 5, 512),      # odd pass count
+    (3, 22, 12, 8, 6, 1, 128),      # one pass per launch
+]
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+@pytest.mark.parametrize("case", TILE_CASES)
+def test_tile_kernel_is_bitwise_the_pass_kernel(case, precision):
+    """The temporally blocked tile kernel computes passes in another order and
+    place (shared-memory tiles, several passes per launch, ping-pong buffers)
+    but the same point updates: bitwise equal to one launch per pass, for
+    run lengths that leave a partial last launch and for split calls."""
+    from paper_2502_09537_b300.solver import (KGS_OPT_TILE_LX, KGS_OPT_TILE_PASSES,
+                                              KGS_OPT_TILE_T1, KGS_OPT_TILE_T2,
+                                              KGS_OPT_TILE_THREADS)
+    dim, N, T1, T2, LX, passes, threads = case
+    elem = 8 if precision == KGS_FP64 else 4
+    while (2 * passes + 2) * (T2 + 2 * passes) * (T1 + 2 * passes if dim == 3 else 1) * 4 * elem > 227 * 1024:
+        T1, T2 = max(2, T1 // 2), max(2, T2 // 2)   # FP64 points are twice the bytes
+    prob = Problem(dim, N, 7.0, 1.0, 1.1, 0.9, 1.2, 0.01)
+    st = random_state(prob, 70 + N, 0.5)
+    ref = run_gpu(prob, st, 13, precision=precision, kernel=1)
+    with Solver.from_problem(prob, precision) as s:
+        s.set_option(KGS_OPT_KERNEL, 3)
+        if dim == 3:
+            s.set_option(KGS_OPT_TILE_T1, T1)
+        s.set_option(KGS_OPT_TILE_T2, T2)
+        s.set_option(KGS_OPT_TILE_LX, LX)
+        s.set_option(KGS_OPT_TILE_PASSES, passes)
+        s.set_option(KGS_OPT_TILE_THREADS, threads)
+        s.set_state(*copy_state(st))
+        s.step(6)
+        s.step(7)
+        got = s.get_state()
+        inv = s.invariants()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    with Solver.from_problem(prob, precision) as s:
+        s.set_state(*ref)
+        assert s.invariants() == inv
+
+
+def test_tile_kernel_fp64_matches_oracle(orc):
+    w = inputs.gauss_3d(40, 60)
+    gpu = run_gpu(w.prob, w.state, 60, kernel=3)
+    ref = run_oracle(orc, w.prob, w.state, 60)
+    assert rel_err(gpu, ref) <= FP64_BAR
