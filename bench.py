@@ -188,6 +188,122 @@ def run_reference(args):
     }))
 
 
+def run_batch(args):
+    """The 96-instance batch: 64 2D grids N in {128..2048} and 32 3D grids N in
+    {64..256}, random parameters, tau = 5e-4, 500 steps, every instance in the
+    chosen precision, stepped by kgs_batch_step (one launch per colour pass over
+    all instances, replayed from a CUDA graph).  One benchmark step = load every
+    initial state from HBM, 500 steps."""
+    import torch
+    from paper_2502_09537_b300 import build as kbuild
+    from paper_2502_09537_b300 import inputs
+    from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, Batch
+    kbuild.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    precision = KGS_FP64 if args.precision == "fp64" else KGS_FP32
+    elem = 8 if precision == KGS_FP64 else 4
+    specs = inputs.batched_instances()
+    nsteps = specs[0][1]
+    total_bytes = sum(p.points * 4 * elem for p, _, _ in specs)
+    b = Batch(int(total_bytes * 1.05) + (64 << 20))
+    init, ids = [], []
+    for p, _, fn in specs:
+        ids.append(b.add(p, precision))
+        init.append([torch.from_numpy(a).cuda() for a in fn()])
+    torch.cuda.synchronize()
+    points = sum(p.points for p, _, _ in specs)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one():
+        for i, st in zip(ids, init):
+            b.set_state(i, *st, stream=stream)
+        b.step(nsteps, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one()
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        times, kern = [], []
+        l0 = b.launch_count
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                for i, st in zip(ids, init):
+                    b.set_state(i, *st, stream=stream)
+                e1.record(stream)
+                b.step(nsteps, stream=stream)
+                e2.record(stream)
+                stream.synchronize()
+                times.append(e0.elapsed_time(e2))
+                kern.append(e1.elapsed_time(e2))
+        launches = b.launch_count - l0
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * points * nsteps * args.steps / (total_ms * 1e-3)
+    step_launches = 2 * nsteps + 1  # one pass launch per colour pass (one precision)
+    pass_ms = sum(kern) / (args.steps * step_launches)
+    upd_per_launch = points * nsteps / step_launches
+    peaks = measured_peaks()
+    if precision == KGS_FP64:
+        mean_dim_flops = sum(p.points * flops_per_point_update(p.dim) for p, _, _ in specs) / points
+        achieved = upd_per_launch * mean_dim_flops / (pass_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz"}
+    else:
+        achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6400.0),
+                "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6400.0), "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    # end to end: host states in and out
+    host_in = [[torch.from_numpy(a.cpu().numpy()).pin_memory().numpy() for a in st] for st in init]
+    host_out = [[np.empty_like(a) for a in st] for st in host_in]
+    with torch.cuda.stream(stream):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for i, st in zip(ids, host_in):
+            b.set_state(i, *st, stream=stream)
+        b.step(nsteps, stream=stream)
+        for i, out in zip(ids, host_out):
+            b.get_state(i, out, stream=stream)
+        e2e_s = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
+        "data": "synthetic",
+        "config": {"workload": "kgs_batch96", "instances": len(specs), "points": points,
+                   "steps_per_solve": nsteps, "precision": args.precision,
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"{world} independent batch(es), one per GPU"},
+        "roofline": roof,
+        "e2e": {"value": world * points * nsteps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": points * 32, "d2h_bytes_per_step": points * 32},
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "kernel_ms_per_launch": pass_ms,
+    }
+    b.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line))
+
+
 def solve(s, stream, init, nsteps, per_chunk_events=None, step_launches=None):
     """One benchmark step: load the initial state, nsteps DP-AVF2 steps with the
     energy evaluated every ENERGY_EVERY steps.  Returns the invariants seen.
@@ -218,7 +334,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d", "batch"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
@@ -226,6 +342,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
 
     import torch

@@ -152,6 +152,62 @@ const char* kgs_last_error(void);
  * the way to learn why kgs_create / kgs_create_ex returned NULL. */
 int kgs_last_status(void);
 
+/* ---- batches of independent instances -----------------------------------
+ * Many KGS problems of different dimensions, sizes, parameters and precisions
+ * stepped together on one device, each bitwise as if stepped alone (the same
+ * pointwise updates of Eqs. scheme1 / dp-avf-kj-adj in the checkerboard order
+ * of Algorithm 3).  One launch per colour pass and precision covers every
+ * instance (a persistent grid over a work list of 256-point chunks); the
+ * launches of a step call are captured in a CUDA graph and replayed while the
+ * instance set and step counts stay the same.  The batch owns one device arena
+ * of a fixed capacity (the memory budget); instances are placed in it first
+ * fit and their space is returned by kgs_batch_remove. */
+typedef struct kgs_batch* kgs_batch_handle;
+
+#define KGS_BATCH_OPT_CTAS_PER_SM 1  /* persistent CTAs per SM, 1..32 (default 8) */
+#define KGS_BATCH_OPT_GRAPH       2  /* 0 off, 1 capture step calls in a CUDA graph (default 1) */
+
+/* Create a batch on `device` (-1 = current) with an arena of capacity_bytes
+ * (>= 4096).  NULL on error (kgs_last_status / kgs_last_error). */
+kgs_batch_handle kgs_batch_create(int device, int64_t capacity_bytes);
+
+/* Add an instance (arguments as kgs_create_ex; precision KGS_FP64 or
+ * KGS_FP32).  Returns its index (>= 0; indices of removed instances are
+ * reused) or a negative status: KGS_ERR_OOM when no free arena range holds its
+ * 2 * N^d * 16 (FP64) or 8 (FP32) bytes. */
+int64_t kgs_batch_add(kgs_batch_handle b, int dim, int64_t N, double L, double kappa1,
+                      double kappa2, double mu, double gamma, double tau, int precision);
+
+/* Remove an instance and return its arena range. */
+int kgs_batch_remove(kgs_batch_handle b, int64_t id);
+
+/* Largest free contiguous arena range in bytes (negative status on error). */
+int64_t kgs_batch_free_bytes(kgs_batch_handle b);
+
+/* State in / out of one instance; arguments and behaviour as kgs_set_state /
+ * kgs_get_state (host buffers use a temporary device staging buffer). */
+int kgs_batch_set_state(kgs_batch_handle b, int64_t id, const double* P, const double* Q,
+                        const double* U, const double* V, int where, void* stream);
+int kgs_batch_get_state(kgs_batch_handle b, int64_t id, double* P, double* Q, double* U,
+                        double* V, int where, void* stream);
+
+/* Advance live instance i by nsteps[i] >= 0 full DP-AVF2 steps (array indexed
+ * by instance index, entries of removed indices ignored), asynchronously on
+ * stream.  Every stepped instance must have a state. */
+int kgs_batch_step_each(kgs_batch_handle b, const int64_t* nsteps, void* stream);
+
+/* Advance every live instance by nsteps. */
+int kgs_batch_step(kgs_batch_handle b, int64_t nsteps, void* stream);
+
+/* Invariants of one instance (as kgs_invariants; synchronises stream). */
+int kgs_batch_invariants(kgs_batch_handle b, int64_t id, double* out3, void* stream);
+
+int kgs_batch_set_option(kgs_batch_handle b, int option, int64_t value);
+int64_t kgs_batch_launch_count(kgs_batch_handle b);
+
+/* Free the arena and every device buffer of the batch.  NULL is ignored. */
+void kgs_batch_destroy(kgs_batch_handle b);
+
 /* ---- allocation-free invariants (no counterpart in the paper) ----------
  * The same three values as kgs_invariants (E_h, S_E, mass), for callers that
  * cannot allocate device memory where they need them: code whose GPU memory

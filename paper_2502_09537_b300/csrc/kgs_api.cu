@@ -101,36 +101,8 @@ bool is_finite_(double x) { return std::isfinite(x); }
 
 void compute_coef(kgs_solver* h)
 {
-    // Half step s = tau/2; coefficients of Eq. scheme1 written for dimension d
-    // (kgs_point.cuh).  Everything in FP64; FP32 handles round the results.
-    const double s = h->tau / 2.0;
-    const double h2 = h->h * h->h;
-    const double d = (double)h->dim;
-    const double beta = s * h->kappa1 / (2.0 * h2);
-    const double B = s * h->kappa2 / h2;
-    const double A = d * B + s * h->mu * h->mu / 2.0;
-    const double E = s * h->gamma;
-    const double inv_det = 1.0 / (1.0 + A * s / 2.0);
-    Coef<double> c;
-    c.alpha = d * beta;
-    c.g = s * h->gamma / 2.0;
-    c.beta = beta;
-    c.Bp = B * inv_det;
-    c.Ep = E * inv_det;
-    c.twoAp = 2.0 * A * inv_det;
-    c.s = s;
-    c.hs = s / 2.0;
-    h->cd = c;
-    Coef<float> f;
-    f.alpha = (float)c.alpha;
-    f.g = (float)c.g;
-    f.beta = (float)c.beta;
-    f.Bp = (float)c.Bp;
-    f.Ep = (float)c.Ep;
-    f.twoAp = (float)c.twoAp;
-    f.s = (float)c.s;
-    f.hs = (float)c.hs;
-    h->cf = f;
+    h->cd = host_coef64(h->dim, h->N, h->L, h->kappa1, h->kappa2, h->mu, h->gamma, h->tau);
+    h->cf = host_coef32(h->cd);
 }
 
 void drop_graph(kgs_solver* h)

@@ -1,0 +1,740 @@
+// kgs_batch.cu -- many independent KGS instances of different sizes,
+// dimensions and precisions stepped together (declared in include/kgs.h,
+// kgs_batch_*).
+//
+// Storage: one device arena per batch, of a capacity fixed at creation (the
+// HBM budget), holding every instance's (P,Q) and (U,V) vec2 arrays; instances
+// are placed first-fit and their space is returned on removal, so a caller can
+// admit new instances as others finish.
+//
+// Stepping: a DP-AVF2 step of every instance is two colour passes (kgs_point.cuh:
+// RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ).  One launch
+// per precision applies one pass to all instances: a persistent grid of CTAs
+// walks a work list of 256-point chunks of every instance's points of that
+// colour.  Each instance i may run its own number of steps n_i; launch g
+// applies pass g of an instance's run while g <= 2 n_i and skips it after.  The
+// launches of a kgs_batch_step_each call are captured once into a CUDA graph
+// and replayed while the instance set and step counts stay the same.  Every
+// point update is the code of a solo run with the same neighbour order, so
+// each instance's state is bitwise that of stepping it alone.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/kgs.h"
+#include "kgs_internal.h"
+
+using namespace kgs;
+
+namespace {
+
+constexpr int kChunk = 256;  // colour points per work item (= CTA size)
+
+template <typename T> struct BatchInst {
+    vec2_t<T>* pq;
+    vec2_t<T>* uv;
+    int dim, N;
+    int64_t half;         // points of one colour
+    int64_t first_chunk;  // prefix of chunks over the instances of this list
+    int64_t nsteps;       // steps of the current call (0: idle)
+    Coef<T> coef;
+};
+
+__device__ __forceinline__ int batch_mode(int64_t g, int64_t n)
+{
+    if (g == 0) return RED_BASE;
+    if (g == 2 * n) return RED_ADJ;
+    return (g & 1) ? BLACK_FUSED : RED_FUSED;
+}
+
+// Linear index and neighbours of the t-th point of a colour (0-based index sum
+// parity `parity`) -- the same point order and neighbour order as the solo
+// pass kernel; rows along the last axis, N/2 points of each colour per row.
+template <int D>
+__device__ __forceinline__ int64_t batch_point(int64_t t, int N, int parity, int64_t nb[2 * D])
+{
+    const int hN = N >> 1;
+    const int64_t row = t / hN;
+    const int kk = (int)(t - row * hN);
+    int i0 = 0, i1 = 0, rp = 0;
+    if (D == 2) {
+        i0 = (int)row;
+        rp = i0 & 1;
+    } else if (D == 3) {
+        i0 = (int)(row / N);
+        i1 = (int)(row - (int64_t)i0 * N);
+        rp = (i0 + i1) & 1;
+    }
+    const int k = 2 * kk + ((parity - rp) & 1);
+    const int64_t n = N;
+    const int64_t i = row * n + k;
+    const int64_t km = (k == 0) ? i + (n - 1) : i - 1;
+    const int64_t kp = (k == N - 1) ? i - (n - 1) : i + 1;
+    if (D == 1) {
+        nb[0] = km;
+        nb[1] = kp;
+    } else if (D == 2) {
+        nb[0] = (i0 == 0) ? i + (n - 1) * n : i - n;
+        nb[1] = (i0 == N - 1) ? i - (n - 1) * n : i + n;
+        nb[2] = km;
+        nb[3] = kp;
+    } else {
+        const int64_t n2 = n * n;
+        nb[0] = (i0 == 0) ? i + (n - 1) * n2 : i - n2;
+        nb[1] = (i0 == N - 1) ? i - (n - 1) * n2 : i + n2;
+        nb[2] = (i1 == 0) ? i + (n - 1) * n : i - n;
+        nb[3] = (i1 == N - 1) ? i - (n - 1) * n : i + n;
+        nb[4] = km;
+        nb[5] = kp;
+    }
+    return i;
+}
+
+template <typename T, int D, int MODE>
+__device__ __forceinline__ void batch_update(const BatchInst<T>& in, int64_t t, int parity)
+{
+    int64_t nb[2 * D];
+    const int64_t i = batch_point<D>(t, in.N, parity, nb);
+    const T* u = reinterpret_cast<const T*>(in.uv);
+    vec2_t<T> a0 = __ldg(&in.pq[nb[0]]);
+    T sp = a0.x, sq = a0.y, su = __ldg(&u[2 * nb[0]]);
+#pragma unroll
+    for (int m = 1; m < 2 * D; ++m) {
+        const vec2_t<T> b = __ldg(&in.pq[nb[m]]);
+        sp = add_(sp, b.x);
+        sq = add_(sq, b.y);
+        su = add_(su, __ldg(&u[2 * nb[m]]));
+    }
+    vec2_t<T> a = in.pq[i];
+    vec2_t<T> b = in.uv[i];
+    update_point<T, MODE>(in.coef, sp, sq, su, a.x, a.y, b.x, b.y);
+    in.pq[i] = a;
+    in.uv[i] = b;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void batch_dispatch(const BatchInst<T>& in, int64_t t, int parity,
+                                               int mode)
+{
+    switch (mode) {
+    case RED_BASE: batch_update<T, D, RED_BASE>(in, t, parity); break;
+    case BLACK_FUSED: batch_update<T, D, BLACK_FUSED>(in, t, parity); break;
+    case RED_FUSED: batch_update<T, D, RED_FUSED>(in, t, parity); break;
+    default: batch_update<T, D, RED_ADJ>(in, t, parity); break;
+    }
+}
+
+// Pass g (colour: red for even g) of every instance of the list.
+template <typename T>
+__global__ void __launch_bounds__(kChunk) batch_pass_kernel(const BatchInst<T>* __restrict__ insts,
+                                                            int ninst, int64_t total_chunks,
+                                                            int64_t g)
+{
+    __shared__ int s_inst;
+    for (int64_t ch = blockIdx.x; ch < total_chunks; ch += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = ninst - 1;  // last instance whose first chunk <= ch
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (insts[mid].first_chunk <= ch) lo = mid;
+                else hi = mid - 1;
+            }
+            s_inst = lo;
+        }
+        __syncthreads();
+        const BatchInst<T>& in = insts[s_inst];
+        __syncthreads();  // s_inst is rewritten in the next iteration
+        if (g > 2 * in.nsteps) continue;
+        const int mode = batch_mode(g, in.nsteps);
+        const int red = red_parity(in.dim);
+        const int parity = (g & 1) ? (red ^ 1) : red;
+        const int64_t t = (ch - in.first_chunk) * kChunk + threadIdx.x;
+        if (t >= in.half) continue;
+        if (in.dim == 1) batch_dispatch<T, 1>(in, t, parity, mode);
+        else if (in.dim == 2) batch_dispatch<T, 2>(in, t, parity, mode);
+        else batch_dispatch<T, 3>(in, t, parity, mode);
+    }
+}
+
+thread_local char g_batch_err[256];
+
+int bfail(int status, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_batch_err, sizeof g_batch_err, fmt, ap);
+    va_end(ap);
+    return report_error(status, g_batch_err);
+}
+
+struct HostInst {
+    bool live = false;
+    int dim = 0, precision = 64;
+    int64_t N = 0, M = 0;
+    double L = 0, kappa1 = 0, kappa2 = 0, mu = 0, gamma = 0, tau = 0;
+    size_t off = 0, bytes = 0;  // arena range: (P,Q) array then (U,V) array
+    bool state_set = false;
+};
+
+}  // namespace
+
+struct kgs_batch {
+    int device = 0;
+    char* arena = nullptr;
+    size_t capacity = 0;
+    std::map<size_t, size_t> free_ranges;  // offset -> length
+    std::vector<HostInst> inst;
+    // device descriptors and work list per precision
+    BatchInst<double>* d64 = nullptr;
+    BatchInst<float>* d32 = nullptr;
+    int cap64 = 0, cap32 = 0;
+    // stepping
+    int ctas_per_sm = 8;
+    int use_graph = 1;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int64_t> graph_key;  // step counts the graph was captured for
+    cudaStream_t capture_stream = nullptr;
+    int64_t launches = 0;
+    int sticky = 0;
+    double* scratch = nullptr;  // invariants partials
+    double* out_dev = nullptr;
+    double* out_host = nullptr;
+    int scratch_blocks = 0;
+};
+
+namespace {
+
+struct BatchDevGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit BatchDevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~BatchDevGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int bcuda(kgs_batch* b, cudaError_t e, const char* what)
+{
+    if (b && !b->sticky) b->sticky = (int)e;
+    return bfail(KGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int bcheck(kgs_batch* b)
+{
+    if (!b) return bfail(KGS_ERR_ARG, "NULL batch handle");
+    if (b->sticky)
+        return bfail(KGS_ERR_CUDA, "batch is in error state after: %s",
+                     cudaGetErrorString((cudaError_t)b->sticky));
+    return KGS_OK;
+}
+
+void drop_batch_graph(kgs_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_key.clear();
+}
+
+// first-fit placement in the arena (256-byte aligned ranges)
+bool arena_alloc(kgs_batch* b, size_t bytes, size_t* off)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (auto it = b->free_ranges.begin(); it != b->free_ranges.end(); ++it) {
+        if (it->second >= bytes) {
+            *off = it->first;
+            const size_t rest = it->second - bytes;
+            const size_t roff = it->first + bytes;
+            b->free_ranges.erase(it);
+            if (rest) b->free_ranges[roff] = rest;
+            return true;
+        }
+    }
+    return false;
+}
+
+void arena_free(kgs_batch* b, size_t off, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    auto it = b->free_ranges.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != b->free_ranges.end() && it->first + it->second == next->first) {
+        it->second += next->second;
+        b->free_ranges.erase(next);
+    }
+    if (it != b->free_ranges.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second == it->first) {
+            prev->second += it->second;
+            b->free_ranges.erase(it);
+        }
+    }
+}
+
+Coef<double> coef64(const HostInst& h)
+{
+    return host_coef64(h.dim, h.N, h.L, h.kappa1, h.kappa2, h.mu, h.gamma, h.tau);
+}
+
+Coef<float> coef32(const HostInst& h) { return host_coef32(coef64(h)); }
+
+template <typename T>
+void build_list(kgs_batch* b, const int64_t* nsteps, std::vector<BatchInst<T>>& list,
+                int64_t* total_chunks)
+{
+    list.clear();
+    int64_t chunks = 0;
+    const int prec = sizeof(T) == 8 ? 64 : 32;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        const HostInst& h = b->inst[i];
+        if (!h.live || h.precision != prec || nsteps[i] <= 0) continue;
+        BatchInst<T> d;
+        d.pq = reinterpret_cast<vec2_t<T>*>(b->arena + h.off);
+        d.uv = d.pq + h.M;
+        d.dim = h.dim;
+        d.N = (int)h.N;
+        d.half = h.M / 2;
+        d.first_chunk = chunks;
+        d.nsteps = nsteps[i];
+        if constexpr (sizeof(T) == 8) d.coef = coef64(h);
+        else d.coef = coef32(h);
+        list.push_back(d);
+        chunks += (d.half + kChunk - 1) / kChunk;
+    }
+    *total_chunks = chunks;
+}
+
+template <typename T>
+int upload_list(kgs_batch* b, const std::vector<BatchInst<T>>& list, cudaStream_t s)
+{
+    BatchInst<T>*& dev = (sizeof(T) == 8) ? reinterpret_cast<BatchInst<T>*&>(b->d64)
+                                          : reinterpret_cast<BatchInst<T>*&>(b->d32);
+    int& cap = (sizeof(T) == 8) ? b->cap64 : b->cap32;
+    if ((int)list.size() > cap) {
+        cudaFree(dev);
+        dev = nullptr;
+        cap = 0;
+        const int want = std::max<int>((int)list.size(), 64);
+        cudaError_t e = cudaMalloc(&dev, want * sizeof(BatchInst<T>));
+        if (e != cudaSuccess) return bcuda(b, e, "batch descriptor allocation");
+        cap = want;
+    }
+    if (!list.empty()) {
+        cudaError_t e = cudaMemcpyAsync(dev, list.data(), list.size() * sizeof(BatchInst<T>),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch descriptor upload");
+        // the host vector must outlive the copy
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch descriptor upload");
+    }
+    return KGS_OK;
+}
+
+template <typename T>
+int launch_batch_pass(kgs_batch* b, int ninst, int64_t chunks, int64_t g, cudaStream_t s)
+{
+    if (ninst == 0 || chunks == 0) return KGS_OK;
+    const BatchInst<T>* dev = (sizeof(T) == 8) ? reinterpret_cast<const BatchInst<T>*>(b->d64)
+                                               : reinterpret_cast<const BatchInst<T>*>(b->d32);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const int64_t grid = std::min<int64_t>(chunks, (int64_t)sms * b->ctas_per_sm);
+    batch_pass_kernel<T><<<(unsigned)grid, kChunk, 0, s>>>(dev, ninst, chunks, g);
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return bcuda(b, e, "batch pass launch");
+    b->launches += 1;
+    return KGS_OK;
+}
+
+int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
+{
+    std::vector<BatchInst<double>> l64;
+    std::vector<BatchInst<float>> l32;
+    int64_t c64 = 0, c32 = 0, nmax = 0;
+    build_list(b, nsteps, l64, &c64);
+    build_list(b, nsteps, l32, &c32);
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (b->inst[i].live) nmax = std::max(nmax, nsteps[i]);
+    if (nmax == 0) return KGS_OK;
+    const int64_t passes = 2 * nmax + 1;
+    std::vector<int64_t> key(nsteps, nsteps + b->inst.size());
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (!b->inst[i].live) key[i] = -1;
+    if (b->use_graph && b->graph && key == b->graph_key) {
+        cudaError_t e = cudaGraphLaunch(b->graph, s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
+        b->launches += passes * ((c64 ? 1 : 0) + (c32 ? 1 : 0));
+        return KGS_OK;
+    }
+    int st = upload_list(b, l64, s);
+    if (!st) st = upload_list(b, l32, s);
+    if (st) return st;
+    if (!b->use_graph) {
+        for (int64_t g = 0; g < passes; ++g) {
+            if ((st = launch_batch_pass<double>(b, (int)l64.size(), c64, g, s))) return st;
+            if ((st = launch_batch_pass<float>(b, (int)l32.size(), c32, g, s))) return st;
+        }
+        return KGS_OK;
+    }
+    drop_batch_graph(b);
+    if (!b->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bcuda(b, e, "cudaStreamCreate");
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaStreamBeginCapture");
+    const int64_t before = b->launches;
+    for (int64_t g = 0; g < passes && !st; ++g) {
+        st = launch_batch_pass<double>(b, (int)l64.size(), c64, g, b->capture_stream);
+        if (!st) st = launch_batch_pass<float>(b, (int)l32.size(), c32, g, b->capture_stream);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->capture_stream, &graph);
+    b->launches = before;
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bcuda(b, e, "cudaGraphInstantiate");
+    }
+    b->graph_key = key;
+    e = cudaGraphLaunch(b->graph, s);
+    if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
+    b->launches += passes * ((c64 ? 1 : 0) + (c32 ? 1 : 0));
+    return KGS_OK;
+}
+
+int inst_check(kgs_batch* b, int64_t id)
+{
+    if (id < 0 || id >= (int64_t)b->inst.size() || !b->inst[id].live)
+        return bfail(KGS_ERR_ARG, "no live instance %lld", (long long)id);
+    return KGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kgs_batch_handle kgs_batch_create(int device, int64_t capacity_bytes)
+{
+    if (capacity_bytes < 4096) {
+        bfail(KGS_ERR_ARG, "capacity must be at least 4096 bytes");
+        return nullptr;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        bfail(KGS_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) {
+        bfail(KGS_ERR_CUDA, "cudaGetDevice failed");
+        return nullptr;
+    }
+    if (device >= ndev) {
+        bfail(KGS_ERR_ARG, "device %d out of range", device);
+        return nullptr;
+    }
+    BatchDevGuard guard(device);
+    kgs_batch* b = new (std::nothrow) kgs_batch();
+    if (!b) {
+        bfail(KGS_ERR_OOM, "host allocation failed");
+        return nullptr;
+    }
+    b->device = device;
+    b->capacity = ((size_t)capacity_bytes + 255) & ~(size_t)255;
+    e = cudaMalloc(&b->arena, b->capacity);
+    if (e == cudaSuccess) {
+        b->scratch_blocks = invariants_blocks((int64_t)1 << 40);
+        e = cudaMalloc(&b->scratch, (size_t)b->scratch_blocks * 3 * sizeof(double));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->out_dev, 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->out_host, 3 * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bfail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA,
+              "batch arena of %lld bytes: %s", (long long)capacity_bytes, cudaGetErrorString(e));
+        cudaFree(b->arena);
+        cudaFree(b->scratch);
+        cudaFree(b->out_dev);
+        if (b->out_host) cudaFreeHost(b->out_host);
+        delete b;
+        return nullptr;
+    }
+    b->free_ranges[0] = b->capacity;
+    return b;
+}
+
+int64_t kgs_batch_add(kgs_batch_handle b, int dim, int64_t N, double L, double kappa1,
+                      double kappa2, double mu, double gamma, double tau, int precision)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if (dim < 1 || dim > 3) return bfail(KGS_ERR_ARG, "dim must be 1, 2 or 3");
+    if (N < 4 || (N & 1)) return bfail(KGS_ERR_ODD_N, "N must be even and >= 4");
+    if (N > 65534 || (dim == 3 && N > 4096) || (dim == 1 && N > (1 << 30)))
+        return bfail(KGS_ERR_RANGE, "N out of range");
+    if (!std::isfinite(L) || L <= 0 || !std::isfinite(kappa1) || !std::isfinite(kappa2) ||
+        !std::isfinite(mu) || !std::isfinite(gamma) || !std::isfinite(tau) || tau == 0.0)
+        return bfail(KGS_ERR_ARG, "parameters must be finite, L > 0, tau != 0");
+    if (precision != KGS_FP64 && precision != KGS_FP32)
+        return bfail(KGS_ERR_ARG, "precision must be KGS_FP64 or KGS_FP32");
+    HostInst h;
+    h.live = true;
+    h.dim = dim;
+    h.N = N;
+    h.M = 1;
+    for (int a = 0; a < dim; ++a) h.M *= N;
+    h.L = L;
+    h.kappa1 = kappa1;
+    h.kappa2 = kappa2;
+    h.mu = mu;
+    h.gamma = gamma;
+    h.tau = tau;
+    h.precision = precision;
+    h.bytes = (size_t)h.M * 2 * (precision == 64 ? sizeof(double2) : sizeof(float2));
+    if (!arena_alloc(b, h.bytes, &h.off))
+        return bfail(KGS_ERR_OOM, "instance needs %zu bytes; the arena has no free range that large",
+                     h.bytes);
+    // reuse a dead slot index if any
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (!b->inst[i].live) {
+            b->inst[i] = h;
+            drop_batch_graph(b);
+            return (int64_t)i;
+        }
+    b->inst.push_back(h);
+    drop_batch_graph(b);
+    return (int64_t)b->inst.size() - 1;
+}
+
+int kgs_batch_remove(kgs_batch_handle b, int64_t id)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if ((st = inst_check(b, id))) return st;
+    arena_free(b, b->inst[id].off, b->inst[id].bytes);
+    b->inst[id].live = false;
+    drop_batch_graph(b);
+    return KGS_OK;
+}
+
+int64_t kgs_batch_free_bytes(kgs_batch_handle b)
+{
+    if (!b) return bfail(KGS_ERR_ARG, "NULL batch handle");
+    size_t best = 0;
+    for (auto& r : b->free_ranges) best = std::max(best, r.second);
+    return (int64_t)best;
+}
+
+int kgs_batch_set_state(kgs_batch_handle b, int64_t id, const double* P, const double* Q,
+                        const double* U, const double* V, int where, void* stream)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if ((st = inst_check(b, id))) return st;
+    if (!P || !Q || !U || !V || (where != KGS_HOST && where != KGS_DEVICE))
+        return bfail(KGS_ERR_ARG, "NULL state pointer or bad memory kind");
+    BatchDevGuard guard(b->device);
+    HostInst& h = b->inst[id];
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* src[4] = {P, Q, U, V};
+    double* stage = nullptr;
+    if (where == KGS_HOST) {
+        cudaError_t e = cudaMallocAsync(&stage, (size_t)h.M * sizeof(double), s);
+        if (e != cudaSuccess) return bcuda(b, e, "staging allocation");
+    }
+    for (int f = 0; f < 4; ++f) {
+        const double* d = src[f];
+        if (where == KGS_HOST) {
+            cudaError_t e = cudaMemcpyAsync(stage, src[f], (size_t)h.M * sizeof(double),
+                                            cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return bcuda(b, e, "state upload");
+            d = stage;
+        }
+        char* base = b->arena + h.off;
+        int n;
+        if (h.precision == 64) {
+            double2* dst = reinterpret_cast<double2*>(base) + (f < 2 ? 0 : h.M);
+            n = launch_pack<double>(h.M, dst, f & 1, d, s);
+        } else {
+            float2* dst = reinterpret_cast<float2*>(base) + (f < 2 ? 0 : h.M);
+            n = launch_pack<float>(h.M, dst, f & 1, d, s);
+        }
+        if (n < 0) return bcuda(b, cudaGetLastError(), "pack launch");
+        b->launches += n;
+    }
+    if (where == KGS_HOST) {
+        cudaFreeAsync(stage, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize");
+    }
+    h.state_set = true;
+    return KGS_OK;
+}
+
+int kgs_batch_get_state(kgs_batch_handle b, int64_t id, double* P, double* Q, double* U, double* V,
+                        int where, void* stream)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if ((st = inst_check(b, id))) return st;
+    if (!P || !Q || !U || !V || (where != KGS_HOST && where != KGS_DEVICE))
+        return bfail(KGS_ERR_ARG, "NULL state pointer or bad memory kind");
+    BatchDevGuard guard(b->device);
+    HostInst& h = b->inst[id];
+    if (!h.state_set) return bfail(KGS_ERR_STATE, "instance has no state");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* dst[4] = {P, Q, U, V};
+    double* stage = nullptr;
+    if (where == KGS_HOST) {
+        cudaError_t e = cudaMallocAsync(&stage, (size_t)h.M * sizeof(double), s);
+        if (e != cudaSuccess) return bcuda(b, e, "staging allocation");
+    }
+    for (int f = 0; f < 4; ++f) {
+        double* d = (where == KGS_HOST) ? stage : dst[f];
+        const char* base = b->arena + h.off;
+        int n;
+        if (h.precision == 64) {
+            const double2* src = reinterpret_cast<const double2*>(base) + (f < 2 ? 0 : h.M);
+            n = launch_unpack<double>(h.M, d, src, f & 1, s);
+        } else {
+            const float2* src = reinterpret_cast<const float2*>(base) + (f < 2 ? 0 : h.M);
+            n = launch_unpack<float>(h.M, d, src, f & 1, s);
+        }
+        if (n < 0) return bcuda(b, cudaGetLastError(), "unpack launch");
+        b->launches += n;
+        if (where == KGS_HOST) {
+            cudaError_t e = cudaMemcpyAsync(dst[f], stage, (size_t)h.M * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return bcuda(b, e, "state download");
+        }
+    }
+    if (where == KGS_HOST) {
+        cudaFreeAsync(stage, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize");
+    }
+    return KGS_OK;
+}
+
+int kgs_batch_step_each(kgs_batch_handle b, const int64_t* nsteps, void* stream)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if (!nsteps) return bfail(KGS_ERR_ARG, "NULL step counts");
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        if (!b->inst[i].live) continue;
+        if (nsteps[i] < 0) return bfail(KGS_ERR_ARG, "negative step count for instance %zu", i);
+        if (nsteps[i] > 0 && !b->inst[i].state_set)
+            return bfail(KGS_ERR_STATE, "instance %zu has no state", i);
+    }
+    BatchDevGuard guard(b->device);
+    return batch_run(b, nsteps, (cudaStream_t)stream);
+}
+
+int kgs_batch_step(kgs_batch_handle b, int64_t nsteps, void* stream)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if (nsteps < 0) return bfail(KGS_ERR_ARG, "nsteps must be >= 0");
+    std::vector<int64_t> n(b->inst.size(), nsteps);
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (!b->inst[i].live) n[i] = 0;
+    return kgs_batch_step_each(b, n.data(), stream);
+}
+
+int kgs_batch_invariants(kgs_batch_handle b, int64_t id, double* out3, void* stream)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    if ((st = inst_check(b, id))) return st;
+    if (!out3) return bfail(KGS_ERR_ARG, "NULL output");
+    HostInst& h = b->inst[id];
+    if (!h.state_set) return bfail(KGS_ERR_STATE, "instance has no state");
+    BatchDevGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    InvParams p;
+    const double hh = h.L / (double)h.N;
+    p.kappa1 = h.kappa1;
+    p.kappa2 = h.kappa2;
+    p.mu = h.mu;
+    p.gamma = h.gamma;
+    p.inv_h2 = 1.0 / (hh * hh);
+    p.hd = 1.0;
+    for (int a = 0; a < h.dim; ++a) p.hd *= hh;
+    Grid g{h.dim, h.N, h.M};
+    const int nb = invariants_blocks(h.M);
+    const char* base = b->arena + h.off;
+    int n = (h.precision == 64)
+                ? launch_invariants<double>(g, reinterpret_cast<const double2*>(base),
+                                            reinterpret_cast<const double2*>(base) + h.M, p,
+                                            b->scratch, nb, b->out_dev, s)
+                : launch_invariants<float>(g, reinterpret_cast<const float2*>(base),
+                                           reinterpret_cast<const float2*>(base) + h.M, p,
+                                           b->scratch, nb, b->out_dev, s);
+    if (n < 0) return bcuda(b, cudaGetLastError(), "invariants launch");
+    b->launches += n;
+    cudaError_t e = cudaMemcpyAsync(b->out_host, b->out_dev, 3 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(b, e, "invariants readback");
+    for (int k = 0; k < 3; ++k) out3[k] = b->out_host[k];
+    return KGS_OK;
+}
+
+int kgs_batch_set_option(kgs_batch_handle b, int option, int64_t value)
+{
+    int st = bcheck(b);
+    if (st) return st;
+    switch (option) {
+    case KGS_BATCH_OPT_CTAS_PER_SM:
+        if (value < 1 || value > 32) return bfail(KGS_ERR_ARG, "CTAs per SM take 1..32");
+        b->ctas_per_sm = (int)value;
+        drop_batch_graph(b);
+        return KGS_OK;
+    case KGS_BATCH_OPT_GRAPH:
+        if (value < 0 || value > 1) return bfail(KGS_ERR_ARG, "graph option takes 0 or 1");
+        b->use_graph = (int)value;
+        drop_batch_graph(b);
+        return KGS_OK;
+    default:
+        return bfail(KGS_ERR_ARG, "unknown batch option %d", option);
+    }
+}
+
+int64_t kgs_batch_launch_count(kgs_batch_handle b) { return b ? b->launches : -1; }
+
+void kgs_batch_destroy(kgs_batch_handle b)
+{
+    if (!b) return;
+    {
+        BatchDevGuard guard(b->device);
+        drop_batch_graph(b);
+        if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+        cudaFree(b->arena);
+        cudaFree(b->d64);
+        cudaFree(b->d32);
+        cudaFree(b->scratch);
+        cudaFree(b->out_dev);
+        if (b->out_host) cudaFreeHost(b->out_host);
+    }
+    delete b;
+}
+
+}  // extern "C"

@@ -65,6 +65,45 @@ int launch_invariants(const Grid& g, const vec2_t<T>* pq, const vec2_t<T>* uv,
                       const InvParams& p, double* partials, int nblocks, double* out3,
                       cudaStream_t stream);
 
+// Half-step coefficients of one problem (kgs_point.cuh), computed in FP64 on
+// the host; the FP32 set is the FP64 one rounded.  One definition for the solo
+// and batched paths, so both step an instance with the same constants.
+inline Coef<double> host_coef64(int dim, int64_t N, double L, double kappa1, double kappa2,
+                                double mu, double gamma, double tau)
+{
+    const double hh = L / (double)N;
+    const double s = tau / 2.0, h2 = hh * hh, d = (double)dim;
+    const double beta = s * kappa1 / (2.0 * h2);
+    const double B = s * kappa2 / h2;
+    const double A = d * B + s * mu * mu / 2.0;
+    const double E = s * gamma;
+    const double inv_det = 1.0 / (1.0 + A * s / 2.0);
+    Coef<double> c;
+    c.alpha = d * beta;
+    c.g = s * gamma / 2.0;
+    c.beta = beta;
+    c.Bp = B * inv_det;
+    c.Ep = E * inv_det;
+    c.twoAp = 2.0 * A * inv_det;
+    c.s = s;
+    c.hs = s / 2.0;
+    return c;
+}
+
+inline Coef<float> host_coef32(const Coef<double>& c)
+{
+    Coef<float> f;
+    f.alpha = (float)c.alpha;
+    f.g = (float)c.g;
+    f.beta = (float)c.beta;
+    f.Bp = (float)c.Bp;
+    f.Ep = (float)c.Ep;
+    f.twoAp = (float)c.twoAp;
+    f.s = (float)c.s;
+    f.hs = (float)c.hs;
+    return f;
+}
+
 // Record status and message as the calling thread's last error (what
 // kgs_last_status / kgs_last_error return); returns status.
 int report_error(int status, const char* msg);

@@ -61,7 +61,7 @@ def coords(prob: Problem) -> List[np.ndarray]:
 
 
 def _full(a, prob):
-    return np.ascontiguousarray(np.broadcast_to(a, (prob.N,) * prob.dim), dtype=np.float64)
+    return np.array(np.broadcast_to(a, (prob.N,) * prob.dim), dtype=np.float64, order="C", copy=True)
 
 
 def _r2(prob: Problem) -> np.ndarray:

@@ -56,6 +56,18 @@ SIGNATURES = {
     "kgs_last_status": (ctypes.c_int, []),
     "kgs_invariants_noalloc": (ctypes.c_int, [ctypes.c_int, _c_int64] + [_c_dbl] * 5
                                + [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "kgs_batch_create": (_vp, [ctypes.c_int, _c_int64]),
+    "kgs_batch_add": (_c_int64, [_vp, ctypes.c_int, _c_int64] + [_c_dbl] * 6 + [ctypes.c_int]),
+    "kgs_batch_remove": (ctypes.c_int, [_vp, _c_int64]),
+    "kgs_batch_free_bytes": (_c_int64, [_vp]),
+    "kgs_batch_set_state": (ctypes.c_int, [_vp, _c_int64, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "kgs_batch_get_state": (ctypes.c_int, [_vp, _c_int64, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "kgs_batch_step_each": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64), _vp]),
+    "kgs_batch_step": (ctypes.c_int, [_vp, _c_int64, _vp]),
+    "kgs_batch_invariants": (ctypes.c_int, [_vp, _c_int64, _dp, _vp]),
+    "kgs_batch_set_option": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64]),
+    "kgs_batch_launch_count": (_c_int64, [_vp]),
+    "kgs_batch_destroy": (None, [_vp]),
     # include/kgs_probe.h
     "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
     "kgs_probe_rcp_ulp": (ctypes.c_int, [_c_int64, _c_dbl, _vp, ctypes.POINTER(_c_int64),
@@ -225,3 +237,84 @@ def probe_rcp_ulp(n: int = 1 << 24, rmax: float = 100.0, stream=None):
     if st != 0:
         raise KGSError(st, "reciprocal probe failed")
     return mx.value, nd.value
+
+
+KGS_BATCH_OPT_CTAS_PER_SM = 1
+KGS_BATCH_OPT_GRAPH = 2
+
+
+class Batch:
+    """Independent KGS instances stepped together (kgs_batch_* of kgs.h)."""
+
+    def __init__(self, capacity_bytes: int, device: int = -1):
+        lib = load_library()
+        self._lib = lib
+        h = lib.kgs_batch_create(device, int(capacity_bytes))
+        if not h:
+            raise KGSError(lib.kgs_last_status(), last_error())
+        self._h = ctypes.c_void_p(h)
+        self._shape = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kgs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, prob, precision: int = KGS_FP64) -> int:
+        i = self._lib.kgs_batch_add(self._h, prob.dim, prob.N, prob.L, prob.kappa1, prob.kappa2,
+                                    prob.mu, prob.gamma, prob.tau, precision)
+        if i < 0:
+            raise KGSError(int(i), last_error())
+        self._shape[int(i)] = (prob.N, prob.dim)
+        return int(i)
+
+    def remove(self, i: int):
+        _check(self._lib.kgs_batch_remove(self._h, i))
+        self._shape.pop(i, None)
+
+    def free_bytes(self) -> int:
+        return int(self._lib.kgs_batch_free_bytes(self._h))
+
+    def set_state(self, i: int, P, Q, U, V, stream=None):
+        N, dim = self._shape[i]
+        where, ptrs, _keep = _as_buffers((P, Q, U, V), N, dim)
+        _check(self._lib.kgs_batch_set_state(self._h, i, *ptrs, where, _stream_ptr(stream)))
+
+    def get_state(self, i: int, out=None, stream=None):
+        N, dim = self._shape[i]
+        if out is None:
+            out = tuple(np.empty((N,) * dim) for _ in range(4))
+        where, ptrs, _keep = _as_buffers(out, N, dim)
+        _check(self._lib.kgs_batch_get_state(self._h, i, *ptrs, where, _stream_ptr(stream)))
+        return tuple(out)
+
+    def step(self, nsteps: int, stream=None):
+        _check(self._lib.kgs_batch_step(self._h, int(nsteps), _stream_ptr(stream)))
+
+    def step_each(self, nsteps, stream=None):
+        arr = (ctypes.c_int64 * len(nsteps))(*[int(n) for n in nsteps])
+        _check(self._lib.kgs_batch_step_each(self._h, arr, _stream_ptr(stream)))
+
+    def invariants(self, i: int, stream=None):
+        out = (ctypes.c_double * 3)()
+        _check(self._lib.kgs_batch_invariants(self._h, i, ctypes.cast(out, _dp), _stream_ptr(stream)))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def set_option(self, option: int, value: int):
+        _check(self._lib.kgs_batch_set_option(self._h, int(option), int(value)))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.kgs_batch_launch_count(self._h))
