@@ -304,6 +304,82 @@ def run_batch(args):
         print(json.dumps(line))
 
 
+def run_serve(args):
+    """Continuous-batching serving: Poisson arrivals of solve requests (dim in
+    {1,2,3}, N in [256,8192] / [128,2048]^2 / [64,384]^3, steps uniform in
+    [100, --max-steps], FP32 or FP64 each, parameters as the batched workload),
+    admitted by a 150 GB device-memory budget, states resident on the device.
+    One benchmark step = serving --requests requests from their arrival to
+    their result on the host; value = point-updates/s over the step, with
+    p50/p99 request latency and the worst per-request energy drift."""
+    import torch
+    from paper_2502_09537_b300 import build as kbuild
+    from paper_2502_09537_b300 import serve
+    kbuild.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    budget = 150 * (1 << 30)
+    stream = torch.cuda.Stream()
+    lat, pts, wall, drift_max, turns = [], 0, 0.0, 0.0, 0
+    launches = 0
+    with torch.cuda.stream(stream):
+        with ClockSampler(local) as clk:
+            for k in range(args.warmup + args.steps):
+                reqs = serve.poisson_requests(args.rate, args.requests, seed=SEED_SERVE + 1000 * rank + k,
+                                              step_range=(100, args.max_steps))
+                srv = serve.Server(budget, quantum=100, stream=stream, keep_state=True)
+                for r in reqs:
+                    srv.submit(r)
+                l0 = srv.batch.launch_count
+                t0 = time.perf_counter()
+                res = srv.run()
+                dt = time.perf_counter() - t0
+                if k >= args.warmup:
+                    wall += dt
+                    pts += srv.point_updates
+                    lat += [r.latency for r in res]
+                    drift_max = max(drift_max, max(r.energy_drift for r in res))
+                    turns += srv.turns
+                    launches += srv.batch.launch_count - l0
+                srv.close()
+    if dist:
+        t = torch.tensor([wall], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t.item())
+    value = world * pts / wall
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "kgs_serve", "rate_per_s": args.rate,
+                   "requests_per_step": args.requests, "step_range": [100, args.max_steps],
+                   "budget_bytes": budget, "quantum_steps": 100,
+                   "l2": "inputs are built per request on the host (cold)",
+                   "parallelism": f"{world} independent server(s), one per GPU"},
+        "latency_s": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99)},
+        "requests_per_s": world * len(lat) / wall,
+        "energy_drift_max": drift_max,
+        "e2e": {"value": value, "unit": UNIT,
+                "note": "each request's state goes host->device at admission and back at completion "
+                        "inside the timed region"},
+        "gpu_launches": launches, "clocks": clk.summary(), "turns": turns,
+    }
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+SEED_SERVE = 2502_09537 + 4
+
+
 def solve(s, stream, init, nsteps, per_chunk_events=None, step_launches=None):
     """One benchmark step: load the initial state, nsteps DP-AVF2 steps with the
     energy evaluated every ENERGY_EVERY steps.  Returns the invariants seen.
@@ -334,7 +410,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d", "batch"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d", "batch", "serve"])
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: request arrival rate (1/s)")
+    ap.add_argument("--requests", type=int, default=48, help="serving: requests per timed step")
+    ap.add_argument("--max-steps", type=int, default=1000,
+                    help="serving: upper end of the per-request step range (workload: 10000)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
@@ -345,6 +425,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import torch

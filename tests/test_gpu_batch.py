@@ -86,3 +86,19 @@ def test_batch_arena_reuse_and_budget():
             for x, y in zip(got, want):
                 assert np.array_equal(x, y)
         assert b.free_bytes() > 0
+
+
+def test_autotuned_options_are_bitwise_neutral():
+    """Whatever the tuner picks, the state is the default's, bit for bit."""
+    from paper_2502_09537_b300 import tune
+    prob = Problem(3, 40, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
+    st = random_state(prob, 9, 0.5)
+    for prec in (KGS_FP64, KGS_FP32):
+        opts = tune.Tuner(None).tune(prob, prec, nsteps=4)
+        want, _ = solo(prob, prec, st, 9)
+        with Solver.from_problem(prob, prec) as s:
+            tune.apply(s, opts)
+            s.set_state(*[a.copy() for a in st])
+            s.step(9)
+            for x, y in zip(s.get_state(), want):
+                assert np.array_equal(x, y)
