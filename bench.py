@@ -48,7 +48,8 @@ def flops_per_point_update(dim: int) -> float:
 # DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
 # ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
 # the kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("2d", "fp64"): 134.36e6 + 74.77e6}
+NCU_TRAFFIC = {("2d", "fp64"): 134.40e6 + 73.88e6,   # pass_kernel_fp64_kgs2d_N2048.md
+               ("3d", "fp32"): 2.156e9 + 2.091e9}     # pass_kernel_fp32_kgs3d_N512.md
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), 148 SMs, 2032 MHz maximum SM
@@ -248,11 +249,8 @@ def run_batch(args):
                 times.append(e0.elapsed_time(e2))
                 kern.append(e1.elapsed_time(e2))
         launches = b.launch_count - l0
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2502_09537_b300.dist import max_over_ranks
+    total_ms = max_over_ranks(sum(times), device="cuda")
     value = world * points * nsteps * args.steps / (total_ms * 1e-3)
     step_launches = 2 * nsteps + 1  # one pass launch per colour pass (one precision)
     pass_ms = sum(kern) / (args.steps * step_launches)
@@ -348,10 +346,8 @@ def run_serve(args):
                     turns += srv.turns
                     launches += srv.batch.launch_count - l0
                 srv.close()
-    if dist:
-        t = torch.tensor([wall], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t.item())
+    from paper_2502_09537_b300.dist import max_over_ranks
+    wall = max_over_ranks(wall, device="cuda")
     value = world * pts / wall
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -487,11 +483,8 @@ def main():
                 E0, S0, _ = seen[0]
                 drift = max(drift, max(abs(E - E0) / max(S0, S) for E, S, _ in seen))
         launches = s.launch_count - launches0
-    total_ms = sum(iter_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2502_09537_b300.dist import max_over_ranks
+    total_ms = max_over_ranks(sum(iter_ms), device="cuda")
     pts_per_step = prob.points * work.nsteps
     value = world * pts_per_step * args.steps / (total_ms * 1e-3)
 
