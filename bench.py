@@ -414,6 +414,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -452,6 +454,9 @@ def main():
     from paper_2502_09537_b300.solver import KGS_OPT_PPT, KGS_OPT_THREADS
     if args.threads:
         s.set_option(KGS_OPT_THREADS, args.threads)
+    if args.kernel:
+        from paper_2502_09537_b300.solver import KGS_OPT_KERNEL
+        s.set_option(KGS_OPT_KERNEL, args.kernel)
     if args.ppt:
         s.set_option(KGS_OPT_PPT, args.ppt)
     torch.cuda.synchronize()
@@ -536,7 +541,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
-                   "threads": args.threads or 256, "ppt": args.ppt or 1,
+                   "threads": args.threads or 256, "kernel": args.kernel,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",

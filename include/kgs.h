@@ -64,7 +64,8 @@ extern "C" {
 /* options (kgs_set_option) */
 #define KGS_OPT_KERNEL   1  /* 0 auto, 1 one launch per colour pass, 2 shared-memory resident,
                                3 temporally blocked tiles (dim 2, 3; allocates a second state
-                               buffer of the same size on first use) */
+                               buffer of the same size on first use), 4 persistent grid-stride
+                               colour passes */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
 #define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
 #define KGS_OPT_PPT      4  /* points of one colour per thread in those kernels: 1 only (2 was

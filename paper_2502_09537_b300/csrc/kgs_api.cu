@@ -113,14 +113,17 @@ void drop_graph(kgs_solver* h)
     }
 }
 
+int kernel_choice(const kgs_solver* h);
+
 Grid grid_of(const kgs_solver* h)
 {
     Grid g{h->dim, h->N, h->M};
     g.threads = h->opt_threads;
+    g.persistent = kernel_choice(h) == 4;
     return g;
 }
 
-enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3 };
+enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4 };
 
 // Default tile shape per dimension and precision (measured on B300; the batch
 // autotuner can override it per handle).
@@ -140,8 +143,7 @@ TileParams default_tile(int dim, int precision)
 int kernel_choice(const kgs_solver* h)
 {
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
-    if (h->opt_kernel == K_PASS || h->opt_kernel == K_SMEM || h->opt_kernel == K_TILE)
-        return h->opt_kernel;
+    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_PERSIST) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
     // Measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass beats the
     // temporally blocked tiles in both precisions (FP32: 8.6e10 vs 6.2e10 /
@@ -525,12 +527,13 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     if (st) return st;
     switch (option) {
     case KGS_OPT_KERNEL:
-        if (value < 0 || value > 3) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 3");
+        if (value < 0 || value > 4) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 4");
         if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))
             return fail(KGS_ERR_RANGE, "grid too large for the shared-memory resident kernel");
         if (value == 3 && h->dim < 2)
             return fail(KGS_ERR_ARG, "the tile kernel needs dim 2 or 3");
         h->opt_kernel = (int)value;
+        drop_graph(h);
         return KGS_OK;
     case KGS_OPT_TILE_T1:
     case KGS_OPT_TILE_T2:

@@ -14,7 +14,9 @@
 // colour.  Each instance i may run its own number of steps n_i; launch g
 // applies pass g of an instance's run while g <= 2 n_i and skips it after.  The
 // launches of a kgs_batch_step_each call are captured once into a CUDA graph
-// and replayed while the instance set and step counts stay the same.  Every
+// and replayed while the instance set and step counts stay the same.  The
+// FP64 and FP32 launch sequences run on two streams forked from the caller's
+// (the first bound by the FP64 pipe, the second by DRAM) and join at the end.  Every
 // point update is the code of a solo run with the same neighbour order, so
 // each instance's state is bitwise that of stepping it alone.
 #include <algorithm>
@@ -198,6 +200,8 @@ struct kgs_batch {
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;  // step counts the graph was captured for
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t side = nullptr;            // second stream: the FP32 passes
+    cudaEvent_t fork = nullptr, join = nullptr;
     int64_t launches = 0;
     int sticky = 0;
     double* scratch = nullptr;  // invariants partials
@@ -378,13 +382,38 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     int st = upload_list(b, l64, s);
     if (!st) st = upload_list(b, l32, s);
     if (st) return st;
-    if (!b->use_graph) {
-        for (int64_t g = 0; g < passes; ++g) {
-            if ((st = launch_batch_pass<double>(b, (int)l64.size(), c64, g, s))) return st;
-            if ((st = launch_batch_pass<float>(b, (int)l32.size(), c32, g, s))) return st;
+    // FP64 passes (bound by the FP64 pipe) on the caller's stream, FP32 passes
+    // (bound by DRAM) on a second stream forked from it, so the two precisions
+    // overlap; the side stream joins back before the call's work completes.
+    const bool both = c64 && c32;
+    if (both && !b->side) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bcuda(b, e, "side stream");
+    }
+    auto issue = [&](cudaStream_t main) -> int {
+        cudaStream_t s32 = main;
+        if (both) {
+            cudaError_t e = cudaEventRecord(b->fork, main);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+            if (e != cudaSuccess) return bcuda(b, e, "fork");
+            s32 = b->side;
+        }
+        int r = KGS_OK;
+        for (int64_t g = 0; g < passes && !r; ++g) {
+            r = launch_batch_pass<double>(b, (int)l64.size(), c64, g, main);
+            if (!r) r = launch_batch_pass<float>(b, (int)l32.size(), c32, g, s32);
+        }
+        if (r) return r;
+        if (both) {
+            cudaError_t e = cudaEventRecord(b->join, b->side);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(main, b->join, 0);
+            if (e != cudaSuccess) return bcuda(b, e, "join");
         }
         return KGS_OK;
-    }
+    };
+    if (!b->use_graph) return issue(s);
     drop_batch_graph(b);
     if (!b->capture_stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
@@ -393,10 +422,7 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "cudaStreamBeginCapture");
     const int64_t before = b->launches;
-    for (int64_t g = 0; g < passes && !st; ++g) {
-        st = launch_batch_pass<double>(b, (int)l64.size(), c64, g, b->capture_stream);
-        if (!st) st = launch_batch_pass<float>(b, (int)l32.size(), c32, g, b->capture_stream);
-    }
+    st = issue(b->capture_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->capture_stream, &graph);
     b->launches = before;
@@ -727,6 +753,9 @@ void kgs_batch_destroy(kgs_batch_handle b)
         BatchDevGuard guard(b->device);
         drop_batch_graph(b);
         if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+        if (b->side) cudaStreamDestroy(b->side);
+        if (b->fork) cudaEventDestroy(b->fork);
+        if (b->join) cudaEventDestroy(b->join);
         cudaFree(b->arena);
         cudaFree(b->d64);
         cudaFree(b->d32);

@@ -14,6 +14,7 @@ struct Grid {
     int64_t N;
     int64_t M;
     int threads = 256;  // CTA size of the colour-pass kernels (128, 256 or 512)
+    bool persistent = false;  // grid-stride persistent colour passes
 };
 
 // Largest point count the shared-memory resident kernel takes for state type T

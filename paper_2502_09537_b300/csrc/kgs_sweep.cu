@@ -12,6 +12,8 @@
 //   (kgs_tile.cu)     several passes per launch on shared-memory tiles.
 //   smem_run_kernel   a whole n-step run inside one CTA with the state resident
 //                     in shared memory (small grids: the 1D workloads).
+#include <algorithm>
+
 #include "kgs_internal.h"
 
 namespace kgs {
@@ -159,6 +161,20 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     uv[i] = b;
 }
 
+// Persistent variant: a grid sized so that every thread gets nearly the same
+// number of points (the colour's points walked with a grid stride), which
+// trims the partial last wave of a one-thread-per-point launch.  Its index
+// divisions run beside the FP64 pipe, so it pays off where that pipe binds.
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(256) pass_persistent_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
+                                                              int64_t N, int64_t half, Coef<T> c,
+                                                              int parity)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride)
+        colour_update<T, D, MODE, true>(pq, uv, t, N, parity, c);
+}
+
 template <typename T, int D, int MODE>
 __device__ __forceinline__ void smem_pass(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, int64_t half,
                                           int parity, const Coef<T>& c)
@@ -218,10 +234,48 @@ static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coe
         pass_kernel<T, D, MODE, int64_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity);
 }
 
+// CTAs for the persistent pass: 148 SMs x b CTAs of 256 threads, b in 3..6
+// chosen to minimise the idle fraction of the last grid-stride round.
+static int64_t persistent_ctas(int64_t half)
+{
+    int64_t best = 148 * 4;
+    double best_loss = 2.0;
+    for (int b = 3; b <= 6; ++b) {
+        const double threads = 148.0 * b * 256.0;
+        const double x = (double)half / threads;
+        const double rounds = (double)(int64_t)(x + 0.999999999);
+        const double loss = rounds > 0 ? (rounds - x) / rounds : 1.0;
+        if (loss < best_loss - 1e-3) {
+            best_loss = loss;
+            best = 148 * b;
+        }
+    }
+    return best;
+}
+
+template <typename T, int D, int MODE>
+static void launch_persistent_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                                cudaStream_t s)
+{
+    const int64_t half = g.M >> 1;
+    const int64_t ctas = std::min<int64_t>(persistent_ctas(half), (half + 255) / 256);
+    const int parity = (MODE == BLACK_FUSED) ? (red_parity(D) ^ 1) : red_parity(D);
+    pass_persistent_kernel<T, D, MODE><<<(unsigned)ctas, 256, 0, s>>>(pq, uv, g.N, half, c, parity);
+}
+
 template <typename T, int D>
 static void launch_pass_d(const Grid& g, int mode, vec2_t<T>* pq, vec2_t<T>* uv,
                           const Coef<T>& c, cudaStream_t s)
 {
+    if (g.persistent) {
+        switch (mode) {
+        case RED_BASE: launch_persistent_t<T, D, RED_BASE>(g, pq, uv, c, s); break;
+        case BLACK_FUSED: launch_persistent_t<T, D, BLACK_FUSED>(g, pq, uv, c, s); break;
+        case RED_FUSED: launch_persistent_t<T, D, RED_FUSED>(g, pq, uv, c, s); break;
+        default: launch_persistent_t<T, D, RED_ADJ>(g, pq, uv, c, s); break;
+        }
+        return;
+    }
     switch (mode) {
     case RED_BASE: launch_pass_t<T, D, RED_BASE>(g, pq, uv, c, s); break;
     case BLACK_FUSED: launch_pass_t<T, D, BLACK_FUSED>(g, pq, uv, c, s); break;

@@ -21,6 +21,7 @@ result does not depend on what else was in the mix (tests check bitwise).
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Deque, Dict, List, Optional, Sequence, Tuple
@@ -77,7 +78,7 @@ class _Active:
 class Server:
     def __init__(self, budget_bytes: int, quantum: int = 100, max_slots: int = 256,
                  device: int = -1, clock: Callable[[], float] = time.perf_counter,
-                 stream=None, keep_state: bool = True):
+                 stream=None, keep_state: bool = True, prepare_ahead: int = 8):
         self.batch = Batch(budget_bytes, device)
         self.budget = budget_bytes
         self.quantum = quantum
@@ -91,9 +92,28 @@ class Server:
         self.t0: Optional[float] = None
         self.turns = 0
         self.point_updates = 0
+        # initial states of the next waiting requests are built on host threads
+        # while the GPU steps the admitted ones (numpy releases the GIL)
+        self.prepare_ahead = prepare_ahead
+        self._pool = concurrent.futures.ThreadPoolExecutor(max_workers=4) if prepare_ahead else None
+        self._prepared: Dict[int, concurrent.futures.Future] = {}
 
     def close(self):
+        if self._pool is not None:
+            self._pool.shutdown(wait=True)
+            self._pool = None
         self.batch.close()
+
+    def _prefetch(self):
+        if self._pool is None:
+            return
+        for req in list(self.pending)[:self.prepare_ahead]:
+            if req.rid not in self._prepared:
+                self._prepared[req.rid] = self._pool.submit(req.state)
+
+    def _initial_state(self, req: Request):
+        fut = self._prepared.pop(req.rid, None)
+        return fut.result() if fut is not None else req.state()
 
     def submit(self, req: Request):
         if state_bytes(req.prob, req.precision) + 256 > self.budget:
@@ -112,7 +132,7 @@ class Server:
             if state_bytes(req.prob, req.precision) > self.batch.free_bytes():
                 break  # FIFO: wait for memory
             inst = self.batch.add(req.prob, req.precision)
-            self.batch.set_state(inst, *req.state(), stream=self.stream)
+            self.batch.set_state(inst, *self._initial_state(req), stream=self.stream)
             E0, S0, _ = self.batch.invariants(inst, stream=self.stream)
             self.active[inst] = _Active(req, inst, req.nsteps, E0, S0, self.now())
             self.pending.popleft()
@@ -129,6 +149,7 @@ class Server:
         if self.t0 is None:
             self.t0 = self.clock()
         while self.pending or self.active:
+            self._prefetch()
             self._admit()
             if not self.active:
                 # nothing on the device: wait for the next arrival
@@ -142,6 +163,7 @@ class Server:
                 counts[inst] = min(self.quantum, a.left)
             self.batch.step_each(counts, stream=self.stream)
             self.turns += 1
+            self._prefetch()  # host work overlaps the launches just queued
             for inst, a in list(self.active.items()):
                 n = counts[inst]
                 a.left -= n

@@ -105,8 +105,9 @@ def test_kernel_variants_and_graphs_are_bitwise_equal():
     a = run_gpu(prob, st, 100, kernel=1, graph=1)
     b = run_gpu(prob, st, 100, kernel=1, graph=0)
     c = run_gpu(prob, st, 100, kernel=2)
-    for x, y, z in zip(a, b, c):
-        assert np.array_equal(x, y) and np.array_equal(x, z)
+    d = run_gpu(prob, st, 100, kernel=4)
+    for x, y, z, q in zip(a, b, c, d):
+        assert np.array_equal(x, y) and np.array_equal(x, z) and np.array_equal(x, q)
 
 
 @pytest.mark.parametrize("dim,N", [(2, 66), (3, 18), (1, 2050)])
@@ -129,7 +130,7 @@ def test_launch_shapes_are_bitwise_equal(dim, N, threads, ppt):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 4])
 def test_split_steps_are_bitwise_equal(kernel):
     """kgs_step(a); kgs_step(b) == kgs_step(a+b), across graph boundaries too."""
     prob = Problem(2, 48, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
