@@ -5,7 +5,9 @@
  * whose rate the measured-peaks file does not give.  This probe measures it
  * (and the FP32 rate) the way a roofline denominator is usually taken: many
  * independent fused multiply-add chains per thread, enough CTAs to fill every
- * SM, timed with CUDA events on the given stream.
+ * SM, timed with CUDA events on the given stream.  The other two entry points
+ * expose the float64 reciprocal and neighbour sum of the colour passes so that
+ * tests can check them against IEEE division and the exact sum.
  */
 #ifndef KGS_PROBE_H
 #define KGS_PROBE_H
@@ -35,6 +37,21 @@ int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* st
  * outputs) or -4 if a CUDA call failed. */
 int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
                       int64_t* n_differ);
+
+/* The float64 neighbour sum of the colour passes on n rows of k values
+ * (k = 2, 4 or 6, the 2d neighbours of a point in 1, 2 or 3 dimensions):
+ * x_host holds the rows one after another (n * k doubles, row-major),
+ * out_host receives n sums and exact_host (may be NULL) n flags, 1 where the
+ * sum was formed in the exact integer accumulator (then it is the correctly
+ * rounded sum of the row) and 0 where the left-to-right float64 sum was taken
+ * (an infinite, NaN or subnormal value, a nonzero value more than 71 binades
+ * below the row's largest, or a sum outside the normal range).  Host buffers
+ * are the caller's; the call copies through device memory on the current
+ * device and `stream` and synchronises it.  Returns 0, -1 for a bad argument
+ * (k not 2, 4 or 6, n < 0, NULL x_host/out_host with n > 0), -3 if device
+ * memory could not be allocated or -4 if a CUDA call failed. */
+int kgs_probe_nsum(int k, int64_t n, const double* x_host, double* out_host,
+                   int32_t* exact_host, void* stream);
 
 #ifdef __cplusplus
 }

@@ -102,18 +102,17 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, int64_t t, 
     int64_t nb[2 * D];
     const int64_t i = batch_point<D>(t, in.N, parity, nb);
     const T* u = reinterpret_cast<const T*>(in.uv);
-    vec2_t<T> a0 = __ldg(&in.pq[nb[0]]);
-    T sp = a0.x, sq = a0.y, su = __ldg(&u[2 * nb[0]]);
+    T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
-    for (int m = 1; m < 2 * D; ++m) {
+    for (int m = 0; m < 2 * D; ++m) {
         const vec2_t<T> b = __ldg(&in.pq[nb[m]]);
-        sp = add_(sp, b.x);
-        sq = add_(sq, b.y);
-        su = add_(su, __ldg(&u[2 * nb[m]]));
+        p[m] = b.x;
+        q[m] = b.y;
+        w[m] = __ldg(&u[2 * nb[m]]);
     }
     vec2_t<T> a = in.pq[i];
     vec2_t<T> b = in.uv[i];
-    update_point<T, MODE>(in.coef, sp, sq, su, a.x, a.y, b.x, b.y);
+    update_point<T, MODE>(in.coef, nsum(p), nsum(q), nsum(w), a.x, a.y, b.x, b.y);
     in.pq[i] = a;
     in.uv[i] = b;
 }

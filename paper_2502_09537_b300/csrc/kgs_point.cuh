@@ -79,6 +79,116 @@ __device__ __forceinline__ double rcp_(double a)
 }
 __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 
+// ---------------------------------------------------- neighbour sums --
+// S = the sum of a field over the 2d neighbours of a point (Eq. scheme1's
+// discrete Laplacian without the centre term).
+//
+// FP32: the left-to-right sum.
+//
+// FP64: the correctly rounded sum (round to nearest even of the exact sum),
+// formed without the FP64 pipe.  On this part the FP64 pipe executes two
+// thread-instructions per cycle per SM and bounds the colour passes, while the
+// 32-bit integer pipe (64 per cycle per SM) is nearly idle; the 2d-1 FP64
+// additions per field are 20% (2D) to 29% (3D) of a pass's FP64 instructions.
+// Each value is split into sign, exponent and 53-bit significand, shifted to
+// the largest exponent in a signed 128-bit fixed-point accumulator (the
+// largest significand's leading bit at bit 123, so up to 8 terms cannot
+// overflow and any term within 71 binades of the largest is added exactly),
+// and the exact sum is rounded once.  Where that does not apply -- an input is
+// infinite, NaN or subnormal, a nonzero term lies more than 71 binades below
+// the largest, or the sum is not a normal number -- the left-to-right FP64 sum
+// is taken instead, in a function call so the compiler cannot execute it
+// speculatively for every lane.  A zero sum is -0 only if every term is -0,
+// as in IEEE addition.  The result does not depend on the neighbour order.
+template <int K>
+__device__ __noinline__ double nsum_seq(const double (&v)[K])
+{
+    double s = v[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) s = __dadd_rn(s, v[i]);
+    return s;
+}
+
+template <int K>
+__device__ __forceinline__ double nsum_exact(const double (&v)[K], bool& ok)
+{
+    static_assert(K >= 2 && K <= 8, "2 to 8 terms");
+    uint64_t m[K];
+    int e[K];
+    uint32_t sg[K];
+    int emax = 0;
+    bool allnz = true;
+    ok = true;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const uint64_t b = (uint64_t)__double_as_longlong(v[i]);
+        const int ei = (int)(b >> 52) & 0x7FF;
+        const uint64_t f = b & 0x000FFFFFFFFFFFFFull;
+        ok = ok && (ei != 0x7FF) && (ei != 0 || f == 0);
+        m[i] = ei ? (f | 0x0010000000000000ull) : 0ull;
+        e[i] = ei;
+        sg[i] = (uint32_t)(b >> 63);
+        emax = ei > emax ? ei : emax;
+        allnz = allnz && (b == 0x8000000000000000ull);
+    }
+    // signed 128-bit accumulator (ahi:alo), unit 2^(emax - 1146)
+    uint64_t alo = 0, ahi = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int d = emax - e[i];
+        ok = ok && (m[i] == 0 || d <= 71);
+        const int sh = 71 - d;
+        uint64_t th, tl;
+        if (sh >= 64) { th = m[i] << (sh - 64); tl = 0; }
+        else if (sh > 0) { th = m[i] >> (64 - sh); tl = m[i] << sh; }
+        else { th = 0; tl = sh == 0 ? m[i] : 0; }
+        const uint64_t neg = 0ull - (uint64_t)sg[i];  // two's complement: (t ^ neg) + (neg & 1)
+        const uint64_t xl = tl ^ neg, xh = th ^ neg;
+        const uint64_t l1 = alo + xl;
+        const uint64_t c1 = l1 < alo ? 1ull : 0ull;
+        const uint64_t l2 = l1 + (neg & 1ull);
+        const uint64_t c2 = l2 < l1 ? 1ull : 0ull;
+        alo = l2;
+        ahi = ahi + xh + c1 + c2;
+    }
+    if ((alo | ahi) == 0ull) return allnz ? -0.0 : 0.0;
+    const uint64_t sgn = ahi >> 63;
+    if (sgn) {
+        alo = ~alo + 1ull;
+        ahi = ~ahi + (alo == 0ull ? 1ull : 0ull);
+    }
+    // normalise the magnitude so that its leading one is bit 127
+    const int c = ahi ? __clzll((long long)ahi) : 64 + __clzll((long long)alo);
+    uint64_t h, l;
+    if (c >= 64) { h = alo << (c - 64); l = 0; }
+    else if (c > 0) { h = (ahi << c) | (alo >> (64 - c)); l = alo << c; }
+    else { h = ahi; l = alo; }
+    const int er = emax + 4 - c;  // biased exponent of the sum
+    ok = ok && er >= 1 && er <= 0x7FE;
+    uint64_t M = h >> 11;  // 53 bits with the leading one
+    const uint64_t rb = (h >> 10) & 1ull;
+    const uint64_t st = ((h & 0x3FFull) | l) != 0ull ? 1ull : 0ull;
+    M += rb & (st | (M & 1ull));  // a carry out of M lands in the exponent field
+    const uint64_t bits = (sgn << 63) | ((((uint64_t)(er - 1)) << 52) + M);
+    return __longlong_as_double((long long)bits);
+}
+
+template <int K> __device__ __forceinline__ double nsum(const double (&v)[K])
+{
+    bool ok;
+    double s = nsum_exact<K>(v, ok);
+    if (!ok) s = nsum_seq<K>(v);
+    return s;
+}
+
+template <int K> __device__ __forceinline__ float nsum(const float (&v)[K])
+{
+    float s = v[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) s = __fadd_rn(s, v[i]);
+    return s;
+}
+
 // --------------------------------------------------------- pointwise --
 // Structure that must hold exactly in floating point, not only algebraically:
 // the Psi update is a Cayley transform, (i - r) Psi' = (i + r) Psi - beta S,

@@ -1,6 +1,7 @@
-// kgs_probe.cu -- FMA issue-rate probe (declared in include/kgs_probe.h).
-// No counterpart in the paper: it measures the FP64 pipe rate that bounds the
-// float64 colour passes, for the roofline denominator.
+// kgs_probe.cu -- probes declared in include/kgs_probe.h: the FMA issue rate
+// (the FP64 pipe rate that bounds the float64 colour passes, for the roofline
+// denominator) and the colour passes' float64 reciprocal and neighbour sum
+// exposed for accuracy tests.
 #include "../../include/kgs_probe.h"
 
 #include <cuda_runtime.h>
@@ -75,7 +76,63 @@ __global__ void rcp_ulp_kernel(int64_t n, double rmax, unsigned long long* max_u
     atomicAdd(n_differ, differ);
 }
 
+template <int K>
+__global__ void nsum_kernel(const double* x, int64_t n, double* out, int32_t* exact)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) v[j] = x[i * K + j];
+        bool ok;
+        double s = kgs::nsum_exact<K>(v, ok);
+        if (!ok) s = kgs::nsum_seq<K>(v);
+        out[i] = s;
+        exact[i] = ok ? 1 : 0;
+        // the colour passes' entry point must agree with the two halves
+        if (__double_as_longlong(kgs::nsum<K>(v)) != __double_as_longlong(s)) exact[i] = -1;
+    }
+}
+
 }  // namespace
+
+extern "C" int kgs_probe_nsum(int k, int64_t n, const double* x_host, double* out_host,
+                              int32_t* exact_host, void* stream)
+{
+    if ((k != 2 && k != 4 && k != 6) || n < 0) return -1;
+    if (n == 0) return 0;
+    if (!x_host || !out_host) return -1;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dx = nullptr, *dout = nullptr;
+    int32_t* dex = nullptr;
+    if (cudaMalloc(&dx, (size_t)n * k * sizeof(double)) != cudaSuccess) return -3;
+    if (cudaMalloc(&dout, (size_t)n * sizeof(double)) != cudaSuccess) {
+        cudaFree(dx);
+        return -3;
+    }
+    if (cudaMalloc(&dex, (size_t)n * sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(dx);
+        cudaFree(dout);
+        return -3;
+    }
+    cudaError_t e = cudaMemcpyAsync(dx, x_host, (size_t)n * k * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const int blocks = (int)((n + 255) / 256 < 148 * 8 ? (n + 255) / 256 : 148 * 8);
+        if (k == 2) nsum_kernel<2><<<blocks, 256, 0, s>>>(dx, n, dout, dex);
+        if (k == 4) nsum_kernel<4><<<blocks, 256, 0, s>>>(dx, n, dout, dex);
+        if (k == 6) nsum_kernel<6><<<blocks, 256, 0, s>>>(dx, n, dout, dex);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, dout, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && exact_host)
+        e = cudaMemcpyAsync(exact_host, dex, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dx);
+    cudaFree(dout);
+    cudaFree(dex);
+    return e == cudaSuccess ? 0 : -4;
+}
 
 extern "C" int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
                                  int64_t* n_differ)

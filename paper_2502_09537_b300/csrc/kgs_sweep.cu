@@ -68,20 +68,17 @@ __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t
                                                const int64_t nb[2 * D], T& SP, T& SQ, T& SU)
 {
     const T* u = reinterpret_cast<const T*>(uv);
-    vec2_t<T> a = GLOBAL ? __ldg(&pq[nb[0]]) : pq[nb[0]];
-    T su = GLOBAL ? __ldg(&u[2 * nb[0]]) : u[2 * nb[0]];
-    T sp = a.x, sq = a.y;
+    T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
-    for (int n = 1; n < 2 * D; ++n) {
-        vec2_t<T> b = GLOBAL ? __ldg(&pq[nb[n]]) : pq[nb[n]];
-        T ub = GLOBAL ? __ldg(&u[2 * nb[n]]) : u[2 * nb[n]];
-        sp = add_(sp, b.x);
-        sq = add_(sq, b.y);
-        su = add_(su, ub);
+    for (int n = 0; n < 2 * D; ++n) {
+        const vec2_t<T> b = GLOBAL ? __ldg(&pq[nb[n]]) : pq[nb[n]];
+        p[n] = b.x;
+        q[n] = b.y;
+        w[n] = GLOBAL ? __ldg(&u[2 * nb[n]]) : u[2 * nb[n]];
     }
-    SP = sp;
-    SQ = sq;
-    SU = su;
+    SP = nsum(p);
+    SQ = nsum(q);
+    SU = nsum(w);
 }
 
 template <typename T, int D, int MODE, bool GLOBAL>
@@ -145,18 +142,17 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
         nb[5] = kp;
     }
     const T* u = reinterpret_cast<const T*>(uv);
-    vec2_t<T> a0 = __ldg(&pq[nb[0]]);
-    T sp = a0.x, sq = a0.y, su = __ldg(&u[2 * nb[0]]);
+    T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
-    for (int m = 1; m < 2 * D; ++m) {
+    for (int m = 0; m < 2 * D; ++m) {
         const vec2_t<T> b = __ldg(&pq[nb[m]]);
-        sp = add_(sp, b.x);
-        sq = add_(sq, b.y);
-        su = add_(su, __ldg(&u[2 * nb[m]]));
+        p[m] = b.x;
+        q[m] = b.y;
+        w[m] = __ldg(&u[2 * nb[m]]);
     }
     vec2_t<T> a = pq[i];
     vec2_t<T> b = uv[i];
-    update_point<T, MODE>(c, sp, sq, su, a.x, a.y, b.x, b.y);
+    update_point<T, MODE>(c, nsum(p), nsum(q), nsum(w), a.x, a.y, b.x, b.y);
     pq[i] = a;
     uv[i] = b;
 }

@@ -82,18 +82,17 @@ template <typename T, int D, int MODE>
 __device__ __forceinline__ void tile_point(vec2_t<T>* spq, vec2_t<T>* suv, int own,
                                            const int (&nb)[2 * D], const Coef<T>& c)
 {
-    vec2_t<T> a0 = spq[nb[0]];
-    T sp = a0.x, sq = a0.y, su = suv[nb[0]].x;
+    T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
-    for (int n = 1; n < 2 * D; ++n) {
+    for (int n = 0; n < 2 * D; ++n) {
         const vec2_t<T> b = spq[nb[n]];
-        sp = add_(sp, b.x);
-        sq = add_(sq, b.y);
-        su = add_(su, suv[nb[n]].x);
+        p[n] = b.x;
+        q[n] = b.y;
+        w[n] = suv[nb[n]].x;
     }
     vec2_t<T> a = spq[own];
     vec2_t<T> b = suv[own];
-    update_point<T, MODE>(c, sp, sq, su, a.x, a.y, b.x, b.y);
+    update_point<T, MODE>(c, nsum(p), nsum(q), nsum(w), a.x, a.y, b.x, b.y);
     spq[own] = a;
     suv[own] = b;
 }

@@ -72,6 +72,7 @@ SIGNATURES = {
     "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
     "kgs_probe_rcp_ulp": (ctypes.c_int, [_c_int64, _c_dbl, _vp, ctypes.POINTER(_c_int64),
                                          ctypes.POINTER(_c_int64)]),
+    "kgs_probe_nsum": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -237,6 +238,26 @@ def probe_rcp_ulp(n: int = 1 << 24, rmax: float = 100.0, stream=None):
     if st != 0:
         raise KGSError(st, "reciprocal probe failed")
     return mx.value, nd.value
+
+
+def probe_nsum(x, stream=None):
+    """The colour passes' float64 neighbour sum of each row of x (shape (n, k),
+    k in {2, 4, 6}): (sums, exact) where exact[i] = 1 if row i was summed in
+    the exact integer accumulator (correctly rounded) and 0 if the
+    left-to-right float64 sum was taken."""
+    import numpy as np
+    lib = load_library()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.ndim != 2:
+        raise ValueError("x must be (n, k)")
+    n, k = x.shape
+    out = np.empty(n, dtype=np.float64)
+    exact = np.empty(n, dtype=np.int32)
+    st = lib.kgs_probe_nsum(k, n, x.ctypes.data, out.ctypes.data, exact.ctypes.data,
+                            _stream_ptr(stream))
+    if st != 0:
+        raise KGSError(st, "neighbour-sum probe failed")
+    return out, exact
 
 
 KGS_BATCH_OPT_CTAS_PER_SM = 1
