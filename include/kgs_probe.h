@@ -5,9 +5,10 @@
  * whose rate the measured-peaks file does not give.  This probe measures it
  * (and the FP32 rate) the way a roofline denominator is usually taken: many
  * independent fused multiply-add chains per thread, enough CTAs to fill every
- * SM, timed with CUDA events on the given stream.  The other two entry points
- * expose the float64 reciprocal and neighbour sum of the colour passes so that
- * tests can check them against IEEE division and the exact sum.
+ * SM, timed with CUDA events on the given stream.  The other entry points
+ * expose the float64 reciprocal, neighbour sums and Psi weight of the colour
+ * passes so that tests can check them against IEEE division and exact
+ * arithmetic.
  */
 #ifndef KGS_PROBE_H
 #define KGS_PROBE_H
@@ -38,20 +39,33 @@ int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* st
 int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
                       int64_t* n_differ);
 
-/* The float64 neighbour sum of the colour passes on n rows of k values
+/* The float64 neighbour sums of the colour passes on n rows of k values
  * (k = 2, 4 or 6, the 2d neighbours of a point in 1, 2 or 3 dimensions):
- * x_host holds the rows one after another (n * k doubles, row-major),
- * out_host receives n sums and exact_host (may be NULL) n flags, 1 where the
- * sum was formed in the exact integer accumulator (then it is the correctly
- * rounded sum of the row) and 0 where the left-to-right float64 sum was taken
- * (an infinite, NaN or subnormal value, a nonzero value more than 71 binades
- * below the row's largest, or a sum outside the normal range).  Host buffers
- * are the caller's; the call copies through device memory on the current
- * device and `stream` and synchronises it.  Returns 0, -1 for a bad argument
- * (k not 2, 4 or 6, n < 0, NULL x_host/out_host with n > 0), -3 if device
- * memory could not be allocated or -4 if a CUDA call failed. */
-int kgs_probe_nsum(int k, int64_t n, const double* x_host, double* out_host,
-                   int32_t* exact_host, void* stream);
+ * x_host holds the rows one after another (n * k doubles, row-major).
+ * sum_host receives each row's sum S and scaled_host beta * S as the passes
+ * form them (beta = the Psi neighbour weight; any double here).
+ * exact_host (may be NULL) receives per row bit 0 = S was formed in the exact
+ * integer accumulator (then it is the correctly rounded sum of the row) and
+ * bit 1 = beta S was (then it is beta times the exact sum, rounded once);
+ * where a bit is 0 the left-to-right float64 sum (times beta, rounded) was
+ * taken: an infinite, NaN or subnormal value, a nonzero value more than 71
+ * binades below the row's largest, a zero or subnormal beta, or a result
+ * outside the normal range.  A row whose entry points disagreed with these
+ * halves reads -1.  Host buffers are the caller's; the call copies through
+ * device memory on the current device and `stream` and synchronises it.
+ * Returns 0, -1 for a bad argument (k not 2, 4 or 6, n < 0, a NULL input or
+ * output other than exact_host with n > 0), -3 if device memory could not
+ * be allocated or -4 if a CUDA call failed. */
+int kgs_probe_nsum(int k, int64_t n, const double* x_host, double beta, double* sum_host,
+                   double* scaled_host, int32_t* exact_host, void* stream);
+
+/* The weight w = 1 / (1 + r^2) of the colour passes' float64 Psi update for
+ * n values r_host[i], written to w_host[i] (host buffers, the caller's; the
+ * call copies through device memory on the current device and `stream` and
+ * synchronises it).  Returns 0, -1 for a bad argument (n < 0, NULL buffers
+ * with n > 0), -3 if device memory could not be allocated or -4 if a CUDA
+ * call failed. */
+int kgs_probe_psi_weight(int64_t n, const double* r_host, double* w_host, void* stream);
 
 #ifdef __cplusplus
 }

@@ -81,50 +81,84 @@ __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 
 // ---------------------------------------------------- neighbour sums --
 // S = the sum of a field over the 2d neighbours of a point (Eq. scheme1's
-// discrete Laplacian without the centre term).
+// discrete Laplacian without the centre term), and beta S.
 //
-// FP32: the left-to-right sum.
+// FP32: the left-to-right sum, and beta S as one more rounded product.
 //
-// FP64: the correctly rounded sum (round to nearest even of the exact sum),
+// FP64: the correctly rounded sum (round to nearest even of the exact sum) and
+// the correctly rounded beta S (one rounding of beta times the exact sum),
 // formed without the FP64 pipe.  On this part the FP64 pipe executes two
 // thread-instructions per cycle per SM and bounds the colour passes, while the
-// 32-bit integer pipe (64 per cycle per SM) is nearly idle; the 2d-1 FP64
-// additions per field are 20% (2D) to 29% (3D) of a pass's FP64 instructions.
+// 32-bit integer pipes (64 ALU and 64 multiply-add lanes per cycle per SM)
+// are nearly idle; the 2d-1 FP64 additions per field and the two products
+// beta S are a quarter (2D) to a third (3D) of a pass's FP64 instructions.
 // Each value is split into sign, exponent and 53-bit significand, shifted to
 // the largest exponent in a signed 128-bit fixed-point accumulator (the
 // largest significand's leading bit at bit 123, so up to 8 terms cannot
-// overflow and any term within 71 binades of the largest is added exactly),
-// and the exact sum is rounded once.  Where that does not apply -- an input is
-// infinite, NaN or subnormal, a nonzero term lies more than 71 binades below
-// the largest, or the sum is not a normal number -- the left-to-right FP64 sum
-// is taken instead, in a function call so the compiler cannot execute it
-// speculatively for every lane.  A zero sum is -0 only if every term is -0,
-// as in IEEE addition.  The result does not depend on the neighbour order.
-template <int K>
-__device__ __noinline__ double nsum_seq(const double (&v)[K])
+// overflow and any term within 71 binades of the largest is added exactly).
+// The exact sum is then rounded once, or multiplied exactly by beta's
+// significand (64 x 53 bits) and rounded once.  Where that does not apply --
+// an input is infinite, NaN or subnormal, a nonzero term lies more than 71
+// binades below the largest, beta is zero or subnormal, or the result is not
+// a normal number -- the left-to-right FP64 sum (times beta, rounded) is taken
+// instead, in a function call so that the compiler cannot execute it
+// speculatively for every lane.  A zero sum is -0 only if every term is -0, as
+// in IEEE addition.  The results do not depend on the neighbour order.
+// The fallback: left-to-right sum of the first k of six values, times beta.
+// Values are passed by value so that the colour passes keep them in
+// registers (an array argument would be stored to local memory at every call
+// site, taken or not).
+static __device__ __noinline__ double seq_sum6(int k, double beta, double v0, double v1, double v2,
+                                        double v3, double v4, double v5)
 {
-    double s = v[0];
-#pragma unroll
-    for (int i = 1; i < K; ++i) s = __dadd_rn(s, v[i]);
-    return s;
+    double s = __dadd_rn(v0, v1);
+    if (k > 2) s = __dadd_rn(__dadd_rn(s, v2), v3);
+    if (k > 4) s = __dadd_rn(__dadd_rn(s, v4), v5);
+    return beta == 1.0 ? s : __dmul_rn(beta, s);
 }
 
+template <int K> __device__ __forceinline__ double nsum_seq(const double (&v)[K])
+{
+    static_assert(K == 2 || K == 4 || K == 6, "2, 4 or 6 neighbours");
+    return seq_sum6(K, 1.0, v[0], v[1], v[K > 2 ? 2 : 0], v[K > 2 ? 3 : 0], v[K > 4 ? 4 : 0],
+                    v[K > 4 ? 5 : 0]);
+}
+
+template <int K> __device__ __forceinline__ double nsum_seq_scaled(const double (&v)[K], double beta)
+{
+    static_assert(K == 2 || K == 4 || K == 6, "2, 4 or 6 neighbours");
+    return seq_sum6(K, beta, v[0], v[1], v[K > 2 ? 2 : 0], v[K > 2 ? 3 : 0], v[K > 4 ? 4 : 0],
+                    v[K > 4 ? 5 : 0]);
+}
+
+// The exact sum, normalised: |S| = (h + l 2^-64) 2^(er - 1086) with the
+// leading one of h at bit 63 (er is the biased exponent of S when S is
+// normal), sign sgn; zero = the sum is exactly zero (then negzero = every term
+// is -0).  ok = false where the exact accumulator does not apply.
+struct ExactSum {
+    uint64_t h, l;
+    int er;
+    uint64_t sgn;
+    bool zero, negzero, ok;
+};
+
 template <int K>
-__device__ __forceinline__ double nsum_exact(const double (&v)[K], bool& ok)
+__device__ __forceinline__ ExactSum exact_sum(const double (&v)[K])
 {
     static_assert(K >= 2 && K <= 8, "2 to 8 terms");
+    ExactSum r;
     uint64_t m[K];
     int e[K];
     uint32_t sg[K];
     int emax = 0;
     bool allnz = true;
-    ok = true;
+    r.ok = true;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const uint64_t b = (uint64_t)__double_as_longlong(v[i]);
         const int ei = (int)(b >> 52) & 0x7FF;
         const uint64_t f = b & 0x000FFFFFFFFFFFFFull;
-        ok = ok && (ei != 0x7FF) && (ei != 0 || f == 0);
+        r.ok = r.ok && (ei != 0x7FF) && (ei != 0 || f == 0);
         m[i] = ei ? (f | 0x0010000000000000ull) : 0ull;
         e[i] = ei;
         sg[i] = (uint32_t)(b >> 63);
@@ -136,7 +170,7 @@ __device__ __forceinline__ double nsum_exact(const double (&v)[K], bool& ok)
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const int d = emax - e[i];
-        ok = ok && (m[i] == 0 || d <= 71);
+        r.ok = r.ok && (m[i] == 0 || d <= 71);
         const int sh = 71 - d;
         uint64_t th, tl;
         if (sh >= 64) { th = m[i] << (sh - 64); tl = 0; }
@@ -151,34 +185,78 @@ __device__ __forceinline__ double nsum_exact(const double (&v)[K], bool& ok)
         alo = l2;
         ahi = ahi + xh + c1 + c2;
     }
-    if ((alo | ahi) == 0ull) return allnz ? -0.0 : 0.0;
-    const uint64_t sgn = ahi >> 63;
-    if (sgn) {
+    r.zero = (alo | ahi) == 0ull;
+    r.negzero = allnz;
+    r.sgn = ahi >> 63;
+    if (r.sgn) {
         alo = ~alo + 1ull;
         ahi = ~ahi + (alo == 0ull ? 1ull : 0ull);
     }
     // normalise the magnitude so that its leading one is bit 127
-    const int c = ahi ? __clzll((long long)ahi) : 64 + __clzll((long long)alo);
-    uint64_t h, l;
-    if (c >= 64) { h = alo << (c - 64); l = 0; }
-    else if (c > 0) { h = (ahi << c) | (alo >> (64 - c)); l = alo << c; }
-    else { h = ahi; l = alo; }
-    const int er = emax + 4 - c;  // biased exponent of the sum
-    ok = ok && er >= 1 && er <= 0x7FE;
-    uint64_t M = h >> 11;  // 53 bits with the leading one
-    const uint64_t rb = (h >> 10) & 1ull;
-    const uint64_t st = ((h & 0x3FFull) | l) != 0ull ? 1ull : 0ull;
-    M += rb & (st | (M & 1ull));  // a carry out of M lands in the exponent field
-    const uint64_t bits = (sgn << 63) | ((((uint64_t)(er - 1)) << 52) + M);
-    return __longlong_as_double((long long)bits);
+    const int c = ahi ? __clzll((long long)ahi) : (alo ? 64 + __clzll((long long)alo) : 0);
+    if (c >= 64) { r.h = alo << (c - 64); r.l = 0; }
+    else if (c > 0) { r.h = (ahi << c) | (alo >> (64 - c)); r.l = alo << c; }
+    else { r.h = ahi; r.l = alo; }
+    r.er = emax + 4 - c;
+    return r;
+}
+
+// Round-to-nearest-even of a significand M (53 bits, leading one at bit 52)
+// with round bit rb and sticky st, packed with sign and biased exponent er
+// (1 <= er <= 0x7FE; a carry out of M lands in the exponent field).
+__device__ __forceinline__ double pack_rn(uint64_t sgn, int er, uint64_t M, uint64_t rb, uint64_t st)
+{
+    M += rb & (st | (M & 1ull));
+    return __longlong_as_double((long long)((sgn << 63) | ((((uint64_t)(er - 1)) << 52) + M)));
+}
+
+// S rounded once; ok = false where the caller must take the fallback.
+template <int K> __device__ __forceinline__ double nsum_try(const double (&v)[K], bool& ok)
+{
+    const ExactSum x = exact_sum<K>(v);
+    ok = x.ok && (x.zero || (x.er >= 1 && x.er <= 0x7FE));
+    if (x.zero) return x.negzero ? -0.0 : 0.0;
+    return pack_rn(x.sgn, x.er, x.h >> 11, (x.h >> 10) & 1ull,
+                   ((x.h & 0x3FFull) | x.l) != 0ull ? 1ull : 0ull);
+}
+
+// beta S rounded once; ok as above.
+template <int K>
+__device__ __forceinline__ double nsum_scaled_try(const double (&v)[K], double beta, bool& ok)
+{
+    const ExactSum x = exact_sum<K>(v);
+    const uint64_t bb = (uint64_t)__double_as_longlong(beta);
+    const int eb = (int)(bb >> 52) & 0x7FF;
+    const uint64_t mb = (bb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const uint64_t sgn = x.sgn ^ (bb >> 63);
+    // (h + l 2^-64) mb in [2^115, 2^117): the integer part in (ph:pl), exact,
+    // and whether a fraction remains (the low half of l mb)
+    const uint64_t lh = __umul64hi(x.l, mb), frac = x.l * mb;
+    const uint64_t pl0 = x.h * mb;
+    const uint64_t pl = pl0 + lh;
+    const uint64_t ph = __umul64hi(x.h, mb) + (pl < pl0 ? 1ull : 0ull);
+    const bool top = (ph >> 52) != 0ull;
+    const uint64_t M = top ? ph : (ph << 1) | (pl >> 63);
+    const uint64_t rb = top ? pl >> 63 : (pl >> 62) & 1ull;
+    const uint64_t rest = top ? pl << 1 : pl << 2;
+    const int er = x.er + eb - (top ? 1022 : 1023);
+    ok = x.ok && eb != 0 && eb != 0x7FF && (x.zero || (er >= 1 && er <= 0x7FE));
+    if (x.zero) return (x.negzero ? 1ull : 0ull) ^ (bb >> 63) ? -0.0 : 0.0;
+    return pack_rn(sgn, er, M, rb, (rest | frac) != 0ull ? 1ull : 0ull);
 }
 
 template <int K> __device__ __forceinline__ double nsum(const double (&v)[K])
 {
     bool ok;
-    double s = nsum_exact<K>(v, ok);
-    if (!ok) s = nsum_seq<K>(v);
-    return s;
+    const double r = nsum_try<K>(v, ok);
+    return ok ? r : nsum_seq<K>(v);
+}
+
+template <int K> __device__ __forceinline__ double nsum_scaled(const double (&v)[K], double beta)
+{
+    bool ok;
+    const double r = nsum_scaled_try<K>(v, beta, ok);
+    return ok ? r : nsum_seq_scaled<K>(v, beta);
 }
 
 template <int K> __device__ __forceinline__ float nsum(const float (&v)[K])
@@ -188,6 +266,118 @@ template <int K> __device__ __forceinline__ float nsum(const float (&v)[K])
     for (int i = 1; i < K; ++i) s = __fadd_rn(s, v[i]);
     return s;
 }
+
+template <int K> __device__ __forceinline__ float nsum_scaled(const float (&v)[K], float beta)
+{
+    return __fmul_rn(beta, nsum<K>(v));
+}
+
+// x + x (exact) without the FP64 pipe: one more in the exponent field for a
+// normal x whose double is normal, the significand shifted for zero and
+// subnormals (a carry moves into the exponent field as it should), infinity
+// on overflow, infinities and NaNs kept.
+__device__ __forceinline__ double twice(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+    const uint64_t sign = b & 0x8000000000000000ull;
+    uint64_t r;
+    if (e - 1u < 0x7FDu) r = b + (1ull << 52);
+    else if (e == 0u) r = sign | ((b << 1) & 0x7FFFFFFFFFFFFFFFull);
+    else if (e == 0x7FEu) r = sign | 0x7FF0000000000000ull;
+    else r = b;
+    return __longlong_as_double((long long)r);
+}
+__device__ __forceinline__ float twice(float x) { return __fadd_rn(x, x); }
+
+// ------------------------------------------------------ 1 / (1 + r^2) --
+// The weight w = 1 / (1 + r^2) of the Psi update.
+//
+// FP32: the correctly rounded reciprocal of the rounded 1 + r^2.
+//
+// FP64, off the FP64 pipe (four FMAs and the FP64 reciprocal estimate per
+// Psi prepare otherwise): with r = m 2^(e-1075), the top 64 bits of m^2 come
+// from one 64 x 64 integer product; 1 is added at its fixed-point position,
+// giving a = A 2^(ea-63) with A in [2^63, 2^64) (relative truncation below
+// 2^-62); Y ~ 2^127 / A starts from the FP32 reciprocal estimate of A's top
+// 24 bits (about 22 correct bits) and takes two Newton-Raphson steps
+// Y <- Y + Y (2^127 - A Y) / 2^127 in 64/128-bit integer arithmetic (the
+// error squares: 2^-44, then the 2^-62 of the truncations); w = Y 2^(-64-ea)
+// rounded to nearest.  The result is within one ulp of the exact
+// 1 / (1 + r^2) (faithful; correctly rounded unless the exact value lies
+// within about 2^-61 of a rounding boundary), subnormal results included
+// (|r| > 2^511, where the FP64 1 + r^2 would overflow).  |r| < 2^-27 gives
+// w = 1, the correctly rounded value.  Infinite r gives 0 and NaN gives NaN,
+// by IEEE division in a call.
+static __device__ __noinline__ double psi_weight_fp64(double r) { return 1.0 / __fma_rn(r, r, 1.0); }
+
+__device__ __forceinline__ double psi_weight_try(double r, bool& ok)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(r);
+    const int er = (int)(b >> 52) & 0x7FF;
+    ok = er != 0x7FF;
+    if (er < 996) return 1.0;
+    const uint64_t M = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
+    uint64_t S = __umul64hi(M, M);  // top 64 bits of m^2: r^2 ~ S 2^e2
+    int e2 = 2 * er - 2108;
+    if (!(S >> 63)) {
+        S <<= 1;
+        e2 -= 1;
+    }
+    uint64_t A;
+    int ea;
+    if (e2 >= -63) {  // r^2 >= 1: 1 sits at bit -e2 <= 63, or below bit 0
+        A = e2 <= 0 ? S + (1ull << (-e2)) : S;
+        ea = e2 + 63;
+        if (A < S) {  // carry out of bit 63
+            A = (A >> 1) | 0x8000000000000000ull;
+            ea += 1;
+        }
+    } else {  // r^2 < 1: a in [1, 2)
+        const int k = -e2 - 63;
+        A = 0x8000000000000000ull + (k < 64 ? S >> k : 0ull);
+        ea = 0;
+    }
+    if (A == 0x8000000000000000ull) {  // a is a power of two: w = 2^-ea exactly
+        if (ea <= 1022) return __longlong_as_double((long long)((uint64_t)(1023 - ea) << 52));
+        const int k = 1074 - ea;  // subnormal 2^k 2^-1074; 2^-1075 ties to 0
+        return __longlong_as_double((long long)(k >= 0 ? 1ull << k : 0ull));
+    }
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)(uint32_t)(A >> 40)));
+    const uint32_t fb = __float_as_uint(rf);
+    uint64_t Y = ((fb >> 23) & 0xFFu) >= 104u ? ~0ull
+                                              : (uint64_t)((fb & 0x7FFFFFu) | 0x800000u) << 40;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const uint64_t plo = A * Y, phi = __umul64hi(A, Y);
+        const int64_t dh = (int64_t)(0x8000000000000000ull - phi - (plo != 0ull ? 1ull : 0ull));
+        const uint64_t adh = dh < 0 ? (uint64_t)(-dh) : (uint64_t)dh;
+        const uint64_t corr = __umul64hi(Y, adh << 1);  // Y |D| / 2^127
+        if (dh < 0) Y -= corr;
+        else Y = (Y + corr < Y) ? ~0ull : Y + corr;
+    }
+    // w = Y 2^(-64-ea): biased exponent E = 1022 - ea when normal
+    const int E = 1022 - ea;
+    if (E >= 1)
+        return pack_rn(0ull, E, Y >> 11, (Y >> 10) & 1ull, (Y & 0x3FFull) != 0ull ? 1ull : 0ull);
+    // subnormal: w = F 2^-1074 with F = Y 2^(E-12), rounded to nearest even
+    const int sh = 12 - E;  // >= 12
+    if (sh > 64) return 0.0;
+    uint64_t F = sh == 64 ? 0ull : Y >> sh;
+    const uint64_t rb = (Y >> (sh - 1)) & 1ull;
+    const uint64_t st = (Y & ((1ull << (sh - 1)) - 1ull)) != 0ull ? 1ull : 0ull;
+    F += rb & (st | (F & 1ull));  // a carry into bit 52 gives the least normal
+    return __longlong_as_double((long long)F);
+}
+
+__device__ __forceinline__ double psi_weight(double r)
+{
+    bool ok;
+    const double w = psi_weight_try(r, ok);
+    return ok ? w : psi_weight_fp64(r);
+}
+__device__ __forceinline__ float psi_weight(float r) { return rcp_(fma_(r, r, 1.0f)); }
 
 // --------------------------------------------------------- pointwise --
 // Structure that must hold exactly in floating point, not only algebraically:
@@ -207,18 +397,21 @@ template <typename T> struct PsiPrep {
     T r, r2, w;  // r, 2r, 1/(1 + r^2)
 };
 
-template <typename T> __device__ __forceinline__ PsiPrep<T> psi_prep(const Coef<T>& c, T u)
+// In 3D the integer pipe already carries three 6-term neighbour sums, so
+// there the weight stays on the FP64 pipe (the rounded 1 + r^2 and the
+// refined reciprocal estimate); 1D and 2D take the integer-pipe psi_weight.
+template <typename T, int D> __device__ __forceinline__ PsiPrep<T> psi_prep(const Coef<T>& c, T u)
 {
     PsiPrep<T> pp;
     pp.r = fma_(-c.g, u, c.alpha);
-    pp.r2 = add_(pp.r, pp.r);
-    pp.w = rcp_(fma_(pp.r, pp.r, T(1)));
+    pp.r2 = twice(pp.r);
+    pp.w = D == 3 ? rcp_(fma_(pp.r, pp.r, T(1))) : psi_weight(pp.r);
     return pp;
 }
 
 // dPsi = (2r Psi - beta S) / (i - r):
 //   N = 2r Psi - bS,  dP = (N_im - r N_re) w,  dQ = -(N_re + r N_im) w,
-// with (bSP, bSQ) = beta S computed once per point and pass.
+// with (bSP, bSQ) = beta S formed once per point and pass with the sums.
 template <typename T>
 __device__ __forceinline__ void psi_apply(const PsiPrep<T>& pp, T bSP, T bSQ, T& P, T& Q)
 {
@@ -258,33 +451,33 @@ template <typename T> __device__ __forceinline__ void uv_step(const Coef<T>& c, 
 // into several calls gives bitwise the same state.
 enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3 };
 
-// Update one point of the pass's colour in registers.  SP, SQ, SU are the
-// neighbour sums (neighbours are of the other colour and fixed for the pass).
-template <typename T, int MODE>
-__device__ __forceinline__ void update_point(const Coef<T>& c, T SP, T SQ, T SU,
+// Update one point of the pass's colour in registers.  bSP, bSQ = beta S_P,
+// beta S_Q and SU = S_U from the neighbour sums above (neighbours are of the
+// other colour and fixed for the pass).
+template <typename T, int D, int MODE>
+__device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T SU,
                                              T& P, T& Q, T& U, T& V)
 {
-    const T bSP = mul_(c.beta, SP), bSQ = mul_(c.beta, SQ);
     if (MODE == RED_BASE) {
-        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
+        psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
         uv_step(c, uv_src(c, SU, P, Q), U, V);      // base (U,V) with |Psi^{n+1}|^2
     } else if (MODE == BLACK_FUSED) {
-        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
+        psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
         // base and adjoint (U,V): both use |Psi^{n+1}|^2 of the base half (the
         // adjoint's |Psi^n|^2) and the same neighbours
         const T t = uv_src(c, SU, P, Q);
         uv_step(c, t, U, V);
         uv_step(c, t, U, V);
-        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);  // adjoint Psi with U^{n+1}
+        psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // adjoint Psi with U^{n+1}
     } else if (MODE == RED_FUSED) {
         uv_step(c, uv_src(c, SU, P, Q), U, V);      // adjoint (U,V) with |Psi^n|^2
-        const PsiPrep<T> pp = psi_prep(c, U);
+        const PsiPrep<T> pp = psi_prep<T, D>(c, U);
         psi_apply(pp, bSP, bSQ, P, Q);              // adjoint Psi with U^{n+1}
         psi_apply(pp, bSP, bSQ, P, Q);              // next base Psi: same U, same r
         uv_step(c, uv_src(c, SU, P, Q), U, V);      // next base (U,V)
     } else {  // RED_ADJ
         uv_step(c, uv_src(c, SU, P, Q), U, V);
-        psi_apply(psi_prep(c, U), bSP, bSQ, P, Q);
+        psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);
     }
 }
 

@@ -1,7 +1,7 @@
 // kgs_probe.cu -- probes declared in include/kgs_probe.h: the FMA issue rate
 // (the FP64 pipe rate that bounds the float64 colour passes, for the roofline
-// denominator) and the colour passes' float64 reciprocal and neighbour sum
-// exposed for accuracy tests.
+// denominator) and the colour passes' float64 reciprocal, neighbour sums and
+// Psi weight exposed for accuracy tests.
 #include "../../include/kgs_probe.h"
 
 #include <cuda_runtime.h>
@@ -77,60 +77,90 @@ __global__ void rcp_ulp_kernel(int64_t n, double rmax, unsigned long long* max_u
 }
 
 template <int K>
-__global__ void nsum_kernel(const double* x, int64_t n, double* out, int32_t* exact)
+__global__ void nsum_kernel(const double* x, int64_t n, double beta, double* sum, double* scaled,
+                            int32_t* exact)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double v[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) v[j] = x[i * K + j];
-        bool ok;
-        double s = kgs::nsum_exact<K>(v, ok);
-        if (!ok) s = kgs::nsum_seq<K>(v);
-        out[i] = s;
-        exact[i] = ok ? 1 : 0;
-        // the colour passes' entry point must agree with the two halves
-        if (__double_as_longlong(kgs::nsum<K>(v)) != __double_as_longlong(s)) exact[i] = -1;
+        bool ok1, ok2;
+        double s1 = kgs::nsum_try<K>(v, ok1);
+        double s2 = kgs::nsum_scaled_try<K>(v, beta, ok2);
+        if (!ok1) s1 = kgs::nsum_seq<K>(v);
+        if (!ok2) s2 = kgs::nsum_seq_scaled<K>(v, beta);
+        sum[i] = s1;
+        scaled[i] = s2;
+        int32_t f = (ok1 ? 1 : 0) | (ok2 ? 2 : 0);
+        // the colour passes' entry points must agree with the two halves
+        if (__double_as_longlong(kgs::nsum<K>(v)) != __double_as_longlong(s1)) f = -1;
+        if (__double_as_longlong(kgs::nsum_scaled<K>(v, beta)) != __double_as_longlong(s2)) f = -1;
+        exact[i] = f;
     }
+}
+
+__global__ void psi_weight_kernel(const double* r, int64_t n, double* w)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = kgs::psi_weight(r[i]);
 }
 
 }  // namespace
 
-extern "C" int kgs_probe_nsum(int k, int64_t n, const double* x_host, double* out_host,
-                              int32_t* exact_host, void* stream)
+extern "C" int kgs_probe_psi_weight(int64_t n, const double* r_host, double* w_host, void* stream)
 {
-    if ((k != 2 && k != 4 && k != 6) || n < 0) return -1;
+    if (n < 0) return -1;
     if (n == 0) return 0;
-    if (!x_host || !out_host) return -1;
+    if (!r_host || !w_host) return -1;
     cudaStream_t s = (cudaStream_t)stream;
-    double *dx = nullptr, *dout = nullptr;
-    int32_t* dex = nullptr;
-    if (cudaMalloc(&dx, (size_t)n * k * sizeof(double)) != cudaSuccess) return -3;
-    if (cudaMalloc(&dout, (size_t)n * sizeof(double)) != cudaSuccess) {
-        cudaFree(dx);
-        return -3;
-    }
-    if (cudaMalloc(&dex, (size_t)n * sizeof(int32_t)) != cudaSuccess) {
-        cudaFree(dx);
-        cudaFree(dout);
-        return -3;
-    }
-    cudaError_t e = cudaMemcpyAsync(dx, x_host, (size_t)n * k * sizeof(double), cudaMemcpyHostToDevice, s);
+    double* dev = nullptr;
+    if (cudaMalloc(&dev, 2 * (size_t)n * sizeof(double)) != cudaSuccess) return -3;
+    cudaError_t e = cudaMemcpyAsync(dev, r_host, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const int blocks = (int)((n + 255) / 256 < 148 * 8 ? (n + 255) / 256 : 148 * 8);
-        if (k == 2) nsum_kernel<2><<<blocks, 256, 0, s>>>(dx, n, dout, dex);
-        if (k == 4) nsum_kernel<4><<<blocks, 256, 0, s>>>(dx, n, dout, dex);
-        if (k == 6) nsum_kernel<6><<<blocks, 256, 0, s>>>(dx, n, dout, dex);
+        psi_weight_kernel<<<blocks, 256, 0, s>>>(dev, n, dev + n);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_host, dout, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(w_host, dev + n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dev);
+    return e == cudaSuccess ? 0 : -4;
+}
+
+extern "C" int kgs_probe_nsum(int k, int64_t n, const double* x_host, double beta, double* sum_host,
+                              double* scaled_host, int32_t* exact_host, void* stream)
+{
+    if ((k != 2 && k != 4 && k != 6) || n < 0) return -1;
+    if (n == 0) return 0;
+    if (!x_host || !sum_host || !scaled_host) return -1;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = (size_t)n * k * sizeof(double) + 2 * (size_t)n * sizeof(double) +
+                      (size_t)n * sizeof(int32_t);
+    char* dev = nullptr;
+    if (cudaMalloc(&dev, nb) != cudaSuccess) return -3;
+    double* dx = (double*)dev;
+    double* dsum = dx + (size_t)n * k;
+    double* dscaled = dsum + n;
+    int32_t* dex = (int32_t*)(dscaled + n);
+    cudaError_t e = cudaMemcpyAsync(dx, x_host, (size_t)n * k * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const int blocks = (int)((n + 255) / 256 < 148 * 8 ? (n + 255) / 256 : 148 * 8);
+        if (k == 2) nsum_kernel<2><<<blocks, 256, 0, s>>>(dx, n, beta, dsum, dscaled, dex);
+        if (k == 4) nsum_kernel<4><<<blocks, 256, 0, s>>>(dx, n, beta, dsum, dscaled, dex);
+        if (k == 6) nsum_kernel<6><<<blocks, 256, 0, s>>>(dx, n, beta, dsum, dscaled, dex);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sum_host, dsum, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scaled_host, dscaled, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && exact_host)
         e = cudaMemcpyAsync(exact_host, dex, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(dx);
-    cudaFree(dout);
-    cudaFree(dex);
+    cudaFree(dev);
     return e == cudaSuccess ? 0 : -4;
 }
 

@@ -62,10 +62,11 @@ __device__ __forceinline__ int64_t colour_point(int64_t t, int64_t N, int parity
     return i;
 }
 
-// Neighbour sums in the fixed order of colour_point.
+// beta S_P, beta S_Q and S_U over the neighbours nb of colour_point.
 template <typename T, int D, bool GLOBAL>
 __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t<T>* uv,
-                                               const int64_t nb[2 * D], T& SP, T& SQ, T& SU)
+                                               const int64_t nb[2 * D], const Coef<T>& c,
+                                               T& bSP, T& bSQ, T& SU)
 {
     const T* u = reinterpret_cast<const T*>(uv);
     T p[2 * D], q[2 * D], w[2 * D];
@@ -76,8 +77,8 @@ __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t
         q[n] = b.y;
         w[n] = GLOBAL ? __ldg(&u[2 * nb[n]]) : u[2 * nb[n]];
     }
-    SP = nsum(p);
-    SQ = nsum(q);
+    bSP = nsum_scaled(p, c.beta);
+    bSQ = nsum_scaled(q, c.beta);
     SU = nsum(w);
 }
 
@@ -87,11 +88,11 @@ __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int6
 {
     int64_t nb[2 * D];
     const int64_t i = colour_point<D>(t, N, parity, nb);
-    T SP, SQ, SU;
-    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, SP, SQ, SU);
+    T bSP, bSQ, SU;
+    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, c, bSP, bSQ, SU);
     vec2_t<T> a = pq[i];
     vec2_t<T> b = uv[i];
-    update_point<T, MODE>(c, SP, SQ, SU, a.x, a.y, b.x, b.y);
+    update_point<T, D, MODE>(c, bSP, bSQ, SU, a.x, a.y, b.x, b.y);
     pq[i] = a;
     uv[i] = b;
 }
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     }
     vec2_t<T> a = pq[i];
     vec2_t<T> b = uv[i];
-    update_point<T, MODE>(c, nsum(p), nsum(q), nsum(w), a.x, a.y, b.x, b.y);
+    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum(w), a.x, a.y, b.x, b.y);
     pq[i] = a;
     uv[i] = b;
 }

@@ -72,7 +72,8 @@ SIGNATURES = {
     "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
     "kgs_probe_rcp_ulp": (ctypes.c_int, [_c_int64, _c_dbl, _vp, ctypes.POINTER(_c_int64),
                                          ctypes.POINTER(_c_int64)]),
-    "kgs_probe_nsum": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _vp, _vp, _vp]),
+    "kgs_probe_nsum": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _c_dbl, _vp, _vp, _vp, _vp]),
+    "kgs_probe_psi_weight": (ctypes.c_int, [_c_int64, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -240,11 +241,12 @@ def probe_rcp_ulp(n: int = 1 << 24, rmax: float = 100.0, stream=None):
     return mx.value, nd.value
 
 
-def probe_nsum(x, stream=None):
-    """The colour passes' float64 neighbour sum of each row of x (shape (n, k),
-    k in {2, 4, 6}): (sums, exact) where exact[i] = 1 if row i was summed in
-    the exact integer accumulator (correctly rounded) and 0 if the
-    left-to-right float64 sum was taken."""
+def probe_nsum(x, beta: float = 1.0, stream=None):
+    """The colour passes' float64 neighbour sums of each row of x (shape
+    (n, k), k in {2, 4, 6}): (S, beta*S, exact) where bit 0 of exact[i] says S
+    of row i came from the exact integer accumulator (correctly rounded) and
+    bit 1 that beta*S did (beta times the exact sum, rounded once); otherwise
+    the left-to-right float64 sum (times beta) was taken."""
     import numpy as np
     lib = load_library()
     x = np.ascontiguousarray(x, dtype=np.float64)
@@ -252,12 +254,25 @@ def probe_nsum(x, stream=None):
         raise ValueError("x must be (n, k)")
     n, k = x.shape
     out = np.empty(n, dtype=np.float64)
+    scaled = np.empty(n, dtype=np.float64)
     exact = np.empty(n, dtype=np.int32)
-    st = lib.kgs_probe_nsum(k, n, x.ctypes.data, out.ctypes.data, exact.ctypes.data,
-                            _stream_ptr(stream))
+    st = lib.kgs_probe_nsum(k, n, x.ctypes.data, float(beta), out.ctypes.data, scaled.ctypes.data,
+                            exact.ctypes.data, _stream_ptr(stream))
     if st != 0:
         raise KGSError(st, "neighbour-sum probe failed")
-    return out, exact
+    return out, scaled, exact
+
+
+def probe_psi_weight(r, stream=None):
+    """w = 1 / (1 + r^2) for each value of r as the float64 colour passes form it."""
+    import numpy as np
+    lib = load_library()
+    r = np.ascontiguousarray(r, dtype=np.float64).ravel()
+    w = np.empty_like(r)
+    st = lib.kgs_probe_psi_weight(r.size, r.ctypes.data, w.ctypes.data, _stream_ptr(stream))
+    if st != 0:
+        raise KGSError(st, "Psi weight probe failed")
+    return w
 
 
 KGS_BATCH_OPT_CTAS_PER_SM = 1

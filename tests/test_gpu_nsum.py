@@ -1,15 +1,18 @@
-"""The float64 neighbour sum of the colour passes against the exact sum.
+"""The float64 neighbour sums of the colour passes against exact arithmetic.
 
 Every FP64 colour pass forms S = the sum of a field over the 2d neighbours
-(Eq. scheme1's discrete Laplacian without the centre term).  The kernels form
-it in an exact integer accumulator and round once, so on its fast path the
-result must be bitwise the correctly rounded sum, which Python's math.fsum
-returns (Shewchuk's exact summation); on the rare fallback it must be the
-left-to-right float64 sum.  Rows cover wide exponent spreads, exact and near
-cancellation, ties in the last place, signed zeros, specials and values of the
-size the solver sees.
+(Eq. scheme1's discrete Laplacian without the centre term) and beta S.  The
+kernels form S in an exact integer accumulator and round once, so on that path
+S must be bitwise the correctly rounded sum, which Python's math.fsum returns
+(Shewchuk's exact summation), and beta S must be bitwise beta times the exact
+sum rounded once, which Python's Fraction arithmetic gives (float() of a
+Fraction is correctly rounded).  On the rare fallback they must be the
+left-to-right float64 sum and its rounded product with beta.  Rows cover wide
+exponent spreads, exact and near cancellation, ties in the last place, signed
+zeros, specials and values of the size the solver sees.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -39,11 +42,15 @@ def _rows(k, n, seed):
     return x
 
 
+def _neg_zeros(row):
+    return all(v == 0.0 and math.copysign(1.0, v) < 0 for v in row)
+
+
 def _expected(row, exact):
     if exact:
         s = math.fsum(row)
         if s == 0.0:  # IEEE: a zero sum is -0 only when every term is -0
-            s = -0.0 if all(v == 0.0 and math.copysign(1.0, v) < 0 for v in row) else 0.0
+            s = -0.0 if _neg_zeros(row) else 0.0
         return s
     s = float(row[0])
     for v in row[1:]:
@@ -51,34 +58,95 @@ def _expected(row, exact):
     return s
 
 
-@pytest.mark.parametrize("k", [2, 4, 6])
-def test_neighbour_sum_is_correctly_rounded(k):
-    x = _rows(k, 1 << 16, 2502_09537 + 40 + k)
-    got, exact = probe_nsum(x)
-    assert not (exact == -1).any(), "nsum disagrees with its two halves"
+def _expected_scaled(row, beta, exact):
+    if exact:
+        f = Fraction(beta) * sum(Fraction(v) for v in row)
+        if f == 0:
+            return math.copysign(0.0, (-1.0 if _neg_zeros(row) else 1.0) * math.copysign(1.0, beta))
+        return float(f)
+    return beta * _expected(row, False)
+
+
+def _same(a, b):
+    if math.isnan(a) and math.isnan(b):
+        return True
+    return np.float64(a).view(np.uint64) == np.float64(b).view(np.uint64)
+
+
+@pytest.mark.parametrize("k,beta", [(2, 1.0), (4, 0.30517578125), (4, -0.1234567890123), (6, 7.3e5)])
+def test_neighbour_sum_is_correctly_rounded(k, beta):
+    x = _rows(k, 1 << 15, 2502_09537 + 40 + k)
+    got, scaled, exact = probe_nsum(x, beta)
+    assert not (exact == -1).any(), "nsum entry points disagree with their halves"
     bad = []
     for i in range(x.shape[0]):
-        want = _expected(x[i].tolist(), exact[i] == 1)
-        if math.isnan(want) and math.isnan(got[i]):
-            continue
-        if np.float64(want).view(np.uint64) != np.float64(got[i]).view(np.uint64):
-            bad.append((x[i].tolist(), want, float(got[i]), int(exact[i])))
+        row = x[i].tolist()
+        want = _expected(row, bool(exact[i] & 1))
+        want2 = _expected_scaled(row, beta, bool(exact[i] & 2))
+        if not _same(want, got[i]) or not _same(want2, scaled[i]):
+            bad.append((row, want, float(got[i]), want2, float(scaled[i]), int(exact[i])))
     assert not bad, bad[:5]
-    # the fast path takes every row of finite normal values within 71 binades
-    assert exact.mean() > 0.7
+    # the exact path takes every row of finite normal values within 71 binades
+    assert (exact & 1).mean() > 0.7 and ((exact & 2) > 0).mean() > 0.6
 
 
 def test_neighbour_sum_fast_path_on_solver_like_values():
     rng = np.random.Generator(np.random.PCG64(2502_09537 + 47))
-    base = np.exp(-rng.uniform(0, 30, size=(1 << 16, 1)))
-    x = base * (1 + 0.05 * rng.normal(size=(1 << 16, 4))) + 1e-4 * rng.normal(size=(1 << 16, 4))
-    got, exact = probe_nsum(x)
-    assert exact.mean() > 0.999
+    base = np.exp(-rng.uniform(0, 30, size=(1 << 15, 1)))
+    x = base * (1 + 0.05 * rng.normal(size=(1 << 15, 4))) + 1e-4 * rng.normal(size=(1 << 15, 4))
+    beta = 0.5 * 5e-4 / (2 * (40.0 / 2048) ** 2)
+    got, scaled, exact = probe_nsum(x, beta)
+    assert (exact == 3).mean() > 0.999
+    sel = exact == 3
     want = np.array([math.fsum(r) for r in x.tolist()])
-    sel = exact == 1
+    want2 = np.array([float(Fraction(beta) * sum(Fraction(v) for v in r)) for r in x.tolist()])
     assert np.array_equal(got[sel].view(np.uint64), want[sel].view(np.uint64))
+    assert np.array_equal(scaled[sel].view(np.uint64), want2[sel].view(np.uint64))
+
+
+def test_neighbour_sum_zero_or_subnormal_beta_falls_back():
+    x = np.array([[1.0, 2.0, 3.0, 4.0], [-0.0, -0.0, -0.0, -0.0]])
+    for beta in (0.0, -0.0, 5e-324):
+        got, scaled, exact = probe_nsum(x, beta)
+        assert (exact & 2).sum() == 0
+        assert _same(scaled[0], beta * 10.0) and _same(scaled[1], beta * -0.0)
 
 
 def test_neighbour_sum_empty():
-    got, exact = probe_nsum(np.zeros((0, 4)))
-    assert got.shape == (0,) and exact.shape == (0,)
+    got, scaled, exact = probe_nsum(np.zeros((0, 4)))
+    assert got.shape == (0,) and scaled.shape == (0,) and exact.shape == (0,)
+
+
+def _ulps(a, b):
+    ia = np.float64(a).view(np.int64)
+    ib = np.float64(b).view(np.int64)
+    return abs(int(ia) - int(ib))
+
+
+def test_psi_weight_within_one_ulp_of_exact():
+    """w = 1/(1 + r^2) (Eq. scheme1's Psi update in increment form) as the FP64
+    passes form it on the integer pipes: within one ulp of the exact value
+    everywhere, correctly rounded almost everywhere."""
+    from paper_2502_09537_b300.solver import probe_psi_weight
+    rng = np.random.Generator(np.random.PCG64(2502_09537 + 48))
+    r = np.concatenate([
+        rng.choice([-1.0, 1.0], size=60000) * 2.0 ** rng.uniform(-32, 31, size=60000),
+        rng.uniform(-3, 3, size=20000),
+        np.array([0.0, -0.0, 5e-324, 1e-300, 2.0 ** -27, -2.0 ** -27, 2.0 ** -26.999, 1.0, -1.0,
+                  2.0, 2.0 ** 29, 2.0 ** 30, -2.0 ** 31, 1e10, 2.0 ** 510, 2.0 ** 520, 1e200,
+                  np.inf, -np.inf])])
+    r = np.concatenate([r, rng.choice([-1.0, 1.0], size=6000) * 2.0 ** rng.uniform(30, 545, size=6000)])
+    w = probe_psi_weight(r)
+    assert math.isnan(probe_psi_weight(np.array([np.nan]))[0])
+    worst, exact, where = 0, 0, None
+    for ri, wi in zip(r.tolist(), w.tolist()):
+        if math.isinf(ri):
+            assert wi == 0.0
+            continue
+        want = float(Fraction(1) / (1 + Fraction(ri) ** 2))
+        u = _ulps(wi, want)
+        if u > worst:
+            worst, where = u, (ri, wi, want)
+        exact += u == 0
+    assert worst <= 1, where
+    assert exact / (r.size - 2) > 0.999
