@@ -38,26 +38,24 @@ ENERGY_EVERY = 100
 def flops_per_point_update(dim: int) -> float:
     """FP64-pipe flops of one point-update (one point, one full DP-AVF2 step)
     as the FP64 colour passes execute them (kgs_point.cuh), FMA = 2, add/mul
-    = 1.  Per pass: Psi apply 12, (U,V) source 6, one (U,V) step 7, and per
-    Psi prepare r = alpha - g U (2) plus, in 3D only, 1 + r^2 (2) and the
-    reciprocal refinement (3 FMA = 6; the estimate runs on the MUFU unit).
-    Black pass: 2 prepares + 2 applies + 1 source + 2 steps; red pass:
-    1 prepare + 2 applies + 2 sources + 2 steps.  1D/2D: black 48, red 52,
-    mean 50; 3D: black 64, red 60, mean 62.  The neighbour sums, beta S, 2r
-    and (1D/2D) 1/(1 + r^2) run on the integer pipes."""
-    prep = 2 if dim <= 2 else 10
-    black = 2 * prep + 2 * 12 + 6 + 2 * 7
-    red = prep + 2 * 12 + 2 * 6 + 2 * 7
+    = 1.  Per pass: Psi prepare r = alpha - g U (2), Psi apply 12, (U,V)
+    source 5 (|Psi|^2 3, E'|Psi|^2 + B'S_U 2), one (U,V) step 7.  Black pass:
+    2 prepares + 2 applies + 1 source + 2 steps = 47 flops (25 instructions);
+    red pass: 1 prepare + 2 applies + 2 sources + 2 steps = 50 (27); a
+    point-update is the mean, 48.5, in any dimension.  The neighbour sums,
+    beta S, B' S_U, 2r and 1/(1 + r^2) run on the integer pipes."""
+    black = 2 * 2 + 2 * 12 + 5 + 2 * 7
+    red = 2 + 2 * 12 + 2 * 5 + 2 * 7
     return (black + red) / 2
 
 
 def algorithmic_flops_per_point_update(dim: int) -> float:
     """All flops of the method per point-update, wherever they run, counting
-    a reciprocal as one: neighbour sums 3(2d-1), beta S 2, Psi prepare 6 (r 2,
-    2r 1, 1 + r^2 2, reciprocal 1), Psi apply 12, (U,V) source 6, (U,V) step
-    7.  Black pass 2 + 2x6 + 2x12 + 6 + 2x7 = 58, red pass 2 + 6 + 2x12 +
-    2x6 + 2x7 = 58."""
-    return 3 * (2 * dim - 1) + 58
+    a reciprocal as one: neighbour sums 3(2d-1), beta S 2, B' S_U 1, Psi
+    prepare 6 (r 2, 2r 1, 1 + r^2 2, reciprocal 1), Psi apply 12, (U,V)
+    source 5, (U,V) step 7.  Black pass 3 + 2x6 + 2x12 + 5 + 2x7 = 58, red
+    pass 3 + 6 + 2x12 + 2x5 + 2x7 = 57."""
+    return 3 * (2 * dim - 1) + 57.5
 
 
 # DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
@@ -276,7 +274,7 @@ def run_batch(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
-                "work": "FP64-pipe flops (neighbour sums, beta S, 2r and, in 1D/2D, 1/(1+r^2) run on the integer pipes)"}
+                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r and 1/(1+r^2) run on the integer pipes)"}
     else:
         achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6400.0),
@@ -538,7 +536,7 @@ def main():
                 "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
                 "probe_tflops": 2 * fma_rate / 1e12,
-                "work": "FP64-pipe flops (neighbour sums, beta S, 2r and, in 1D/2D, 1/(1+r^2) run on the integer pipes)",
+                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r and 1/(1+r^2) run on the integer pipes)",
                 "flops_per_point_update": flops_per_point_update(prob.dim),
                 "algorithmic_flops_per_point_update": algorithmic_flops_per_point_update(prob.dim),
                 "algorithmic_tflops": upd_per_launch * algorithmic_flops_per_point_update(prob.dim)

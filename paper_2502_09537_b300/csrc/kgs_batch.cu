@@ -112,7 +112,7 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, int64_t t, 
     }
     vec2_t<T> a = in.pq[i];
     vec2_t<T> b = in.uv[i];
-    update_point<T, D, MODE>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta), nsum(w), a.x, a.y, b.x, b.y);
+    update_point<T, D, MODE>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta), nsum_scaled(w, in.coef.Bp), a.x, a.y, b.x, b.y);
     in.pq[i] = a;
     in.uv[i] = b;
 }

@@ -81,9 +81,10 @@ __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 
 // ---------------------------------------------------- neighbour sums --
 // S = the sum of a field over the 2d neighbours of a point (Eq. scheme1's
-// discrete Laplacian without the centre term), and beta S.
+// discrete Laplacian without the centre term), and c S for a constant c
+// (beta for the Psi fields, B' for U).
 //
-// FP32: the left-to-right sum, and beta S as one more rounded product.
+// FP32: the left-to-right sum, and c S as one more rounded product.
 //
 // FP64: the correctly rounded sum (round to nearest even of the exact sum) and
 // the correctly rounded beta S (one rounding of beta times the exact sum),
@@ -92,18 +93,21 @@ __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 // 32-bit integer pipes (64 ALU and 64 multiply-add lanes per cycle per SM)
 // are nearly idle; the 2d-1 FP64 additions per field and the two products
 // beta S are a quarter (2D) to a third (3D) of a pass's FP64 instructions.
-// Each value is split into sign, exponent and 53-bit significand, shifted to
-// the largest exponent in a signed 128-bit fixed-point accumulator (the
-// largest significand's leading bit at bit 123, so up to 8 terms cannot
-// overflow and any term within 71 binades of the largest is added exactly).
-// The exact sum is then rounded once, or multiplied exactly by beta's
-// significand (64 x 53 bits) and rounded once.  Where that does not apply --
-// an input is infinite, NaN or subnormal, a nonzero term lies more than 71
-// binades below the largest, beta is zero or subnormal, or the result is not
-// a normal number -- the left-to-right FP64 sum (times beta, rounded) is taken
-// instead, in a function call so that the compiler cannot execute it
-// speculatively for every lane.  A zero sum is -0 only if every term is -0, as
-// in IEEE addition.  The results do not depend on the neighbour order.
+// Each value is split into sign, exponent and significand (subnormals exactly,
+// as exponent 1 without the hidden bit), shifted to the largest exponent in a
+// signed 96-bit fixed-point accumulator held in three 32-bit words (the
+// largest significand's leading bit at bit 91, so up to 6 terms cannot
+// overflow and any term within 39 binades of the largest is added exactly)
+// and added with the PTX carry chain (add.cc/addc; a negative term enters as
+// its one's complement with the carry-in set by its sign).  The exact sum is
+// then rounded once, or multiplied exactly by beta's significand (64 x 53
+// bits) and rounded once.  Where that does not apply -- an input is infinite
+// or NaN, a nonzero term lies more than 39 binades below the largest, beta is
+// zero or subnormal, or the result is not a normal number -- the
+// left-to-right FP64 sum (times beta, rounded) is taken instead, in a
+// function call so that the compiler cannot execute it speculatively for
+// every lane.  A zero sum is -0 only if every term is -0, as in IEEE
+// addition.  The results do not depend on the neighbour order.
 // The fallback: left-to-right sum of the first k of six values, times beta.
 // Values are passed by value so that the colour passes keep them in
 // registers (an array argument would be stored to local memory at every call
@@ -142,61 +146,74 @@ struct ExactSum {
     bool zero, negzero, ok;
 };
 
+// (a2:a1:a0) += (x2:x1:x0) + (s & 1), s = 0 or all ones: one carry chain.
+__device__ __forceinline__ void add96_cin(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t x0,
+                                          uint32_t x1, uint32_t x2, uint32_t s)
+{
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %3, %3;\n\t"  // carry = top bit of s
+        "addc.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.u32 %2, %2, %6;\n\t}"
+        : "+r"(a0), "+r"(a1), "+r"(a2)
+        : "r"(s), "r"(x0), "r"(x1), "r"(x2));
+}
+
 template <int K>
 __device__ __forceinline__ ExactSum exact_sum(const double (&v)[K])
 {
-    static_assert(K >= 2 && K <= 8, "2 to 8 terms");
-    ExactSum r;
-    uint64_t m[K];
+    static_assert(K >= 2 && K <= 6, "2 to 6 terms");
+    uint32_t hi[K], lo[K];
     int e[K];
-    uint32_t sg[K];
-    int emax = 0;
+    int emax = 1, emin = 0x7FF;  // largest exponent; smallest of a nonzero term
     bool allnz = true;
-    r.ok = true;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const uint64_t b = (uint64_t)__double_as_longlong(v[i]);
-        const int ei = (int)(b >> 52) & 0x7FF;
-        const uint64_t f = b & 0x000FFFFFFFFFFFFFull;
-        r.ok = r.ok && (ei != 0x7FF) && (ei != 0 || f == 0);
-        m[i] = ei ? (f | 0x0010000000000000ull) : 0ull;
-        e[i] = ei;
-        sg[i] = (uint32_t)(b >> 63);
+        hi[i] = (uint32_t)__double2hiint(v[i]);
+        lo[i] = (uint32_t)__double2loint(v[i]);
+        e[i] = (int)(hi[i] >> 20) & 0x7FF;
+        const int ei = e[i] > 1 ? e[i] : 1;  // subnormal: exponent 1, no hidden bit
         emax = ei > emax ? ei : emax;
-        allnz = allnz && (b == 0x8000000000000000ull);
+        const bool nz = ((hi[i] << 1) | lo[i]) != 0u;
+        emin = (nz && ei < emin) ? ei : emin;
+        allnz = allnz && hi[i] == 0x80000000u && lo[i] == 0u;
     }
-    // signed 128-bit accumulator (ahi:alo), unit 2^(emax - 1146)
-    uint64_t alo = 0, ahi = 0;
+    ExactSum r;
+    r.ok = emax != 0x7FF && emax - emin <= 39;  // holds for all-zero rows (emin = 0x7FF)
+    // signed 96-bit accumulator (a2:a1:a0), unit 2^(emax - 1114)
+    uint32_t a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const int d = emax - e[i];
-        r.ok = r.ok && (m[i] == 0 || d <= 71);
-        const int sh = 71 - d;
-        uint64_t th, tl;
-        if (sh >= 64) { th = m[i] << (sh - 64); tl = 0; }
-        else if (sh > 0) { th = m[i] >> (64 - sh); tl = m[i] << sh; }
-        else { th = 0; tl = sh == 0 ? m[i] : 0; }
-        const uint64_t neg = 0ull - (uint64_t)sg[i];  // two's complement: (t ^ neg) + (neg & 1)
-        const uint64_t xl = tl ^ neg, xh = th ^ neg;
-        const uint64_t l1 = alo + xl;
-        const uint64_t c1 = l1 < alo ? 1ull : 0ull;
-        const uint64_t l2 = l1 + (neg & 1ull);
-        const uint64_t c2 = l2 < l1 ? 1ull : 0ull;
-        alo = l2;
-        ahi = ahi + xh + c1 + c2;
+        const uint32_t mh = (hi[i] & 0xFFFFFu) | (e[i] ? 0x100000u : 0u);
+        const int ei = e[i] > 1 ? e[i] : 1;
+        int sh = 39 - emax + ei;
+        sh = sh > 0 ? sh : 0;  // terms below the window are zeros, or the row is not ok
+        const uint32_t b = (uint32_t)sh & 31u;
+        const uint32_t w0 = lo[i] << b;
+        const uint32_t w1 = __funnelshift_l(lo[i], mh, b);
+        const uint32_t w2 = __funnelshift_l(mh, 0u, b);
+        const bool q = sh >= 32;  // then b <= 7 and w2 = 0
+        const uint32_t s = (uint32_t)((int32_t)hi[i] >> 31);
+        add96_cin(a0, a1, a2, (q ? 0u : w0) ^ s, (q ? w0 : w1) ^ s, (q ? w1 : w2) ^ s, s);
     }
-    r.zero = (alo | ahi) == 0ull;
+    const uint32_t sm = (uint32_t)((int32_t)a2 >> 31);
+    r.sgn = sm & 1u;
+    uint32_t m0 = 0, m1 = 0, m2 = 0;  // magnitude
+    add96_cin(m0, m1, m2, a0 ^ sm, a1 ^ sm, a2 ^ sm, sm);
+    r.zero = (m0 | m1 | m2) == 0u;
     r.negzero = allnz;
-    r.sgn = ahi >> 63;
-    if (r.sgn) {
-        alo = ~alo + 1ull;
-        ahi = ~ahi + (alo == 0ull ? 1ull : 0ull);
-    }
-    // normalise the magnitude so that its leading one is bit 127
-    const int c = ahi ? __clzll((long long)ahi) : (alo ? 64 + __clzll((long long)alo) : 0);
-    if (c >= 64) { r.h = alo << (c - 64); r.l = 0; }
-    else if (c > 0) { r.h = (ahi << c) | (alo >> (64 - c)); r.l = alo << c; }
-    else { r.h = ahi; r.l = alo; }
+    // normalise: the leading word, then the bits below its leading one
+    const bool w2nz = m2 != 0u, w1nz = m1 != 0u;
+    const uint32_t p2 = w2nz ? m2 : (w1nz ? m1 : m0);
+    const uint32_t p1 = w2nz ? m1 : (w1nz ? m0 : 0u);
+    const uint32_t p0 = w2nz ? m0 : 0u;
+    const int cb = __clz((int)p2);
+    const int c = (w2nz ? 0 : (w1nz ? 32 : 64)) + cb;
+    const uint32_t n2 = __funnelshift_l(p1, p2, (uint32_t)cb);
+    const uint32_t n1 = __funnelshift_l(p0, p1, (uint32_t)cb);
+    const uint32_t n0 = p0 << (cb & 31);
+    r.h = ((uint64_t)n2 << 32) | n1;
+    r.l = (uint64_t)n0 << 32;
     r.er = emax + 4 - c;
     return r;
 }
@@ -307,62 +324,51 @@ __device__ __forceinline__ float twice(float x) { return __fadd_rn(x, x); }
 // 1 / (1 + r^2) (faithful; correctly rounded unless the exact value lies
 // within about 2^-61 of a rounding boundary), subnormal results included
 // (|r| > 2^511, where the FP64 1 + r^2 would overflow).  |r| < 2^-27 gives
-// w = 1, the correctly rounded value.  Infinite r gives 0 and NaN gives NaN,
-// by IEEE division in a call.
-static __device__ __noinline__ double psi_weight_fp64(double r) { return 1.0 / __fma_rn(r, r, 1.0); }
+// w = 1, the correctly rounded value.  The common path is branch-free; a
+// subnormal result and non-finite r (infinite r gives 0, NaN gives NaN) are
+// finished in a call.
 
-__device__ __forceinline__ double psi_weight_try(double r, bool& ok)
+// a = A 2^(ea-63) ~ 1 + r^2 for finite r, then Y ~ 2^127 / A: 1/a = Y 2^(-64-ea).
+__device__ __forceinline__ void psi_weight_core(uint64_t b, int er, uint64_t& Y, int& ea)
 {
-    const uint64_t b = (uint64_t)__double_as_longlong(r);
-    const int er = (int)(b >> 52) & 0x7FF;
-    ok = er != 0x7FF;
-    if (er < 996) return 1.0;
     const uint64_t M = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
-    uint64_t S = __umul64hi(M, M);  // top 64 bits of m^2: r^2 ~ S 2^e2
-    int e2 = 2 * er - 2108;
-    if (!(S >> 63)) {
-        S <<= 1;
-        e2 -= 1;
-    }
-    uint64_t A;
-    int ea;
-    if (e2 >= -63) {  // r^2 >= 1: 1 sits at bit -e2 <= 63, or below bit 0
-        A = e2 <= 0 ? S + (1ull << (-e2)) : S;
-        ea = e2 + 63;
-        if (A < S) {  // carry out of bit 63
-            A = (A >> 1) | 0x8000000000000000ull;
-            ea += 1;
-        }
-    } else {  // r^2 < 1: a in [1, 2)
-        const int k = -e2 - 63;
-        A = 0x8000000000000000ull + (k < 64 ? S >> k : 0ull);
-        ea = 0;
-    }
-    if (A == 0x8000000000000000ull) {  // a is a power of two: w = 2^-ea exactly
-        if (ea <= 1022) return __longlong_as_double((long long)((uint64_t)(1023 - ea) << 52));
-        const int k = 1074 - ea;  // subnormal 2^k 2^-1074; 2^-1075 ties to 0
-        return __longlong_as_double((long long)(k >= 0 ? 1ull << k : 0ull));
-    }
+    uint64_t S = __umul64hi(M, M);  // top 64 bits of m^2
+    const bool low = (S >> 63) == 0ull;
+    S = low ? S << 1 : S;
+    const int e2 = 2 * er - 2108 - (low ? 1 : 0);  // r^2 ~ S 2^e2, S in [2^63, 2^64)
+    // r^2 >= 1: 1 sits at bit -e2 <= 63 (or below bit 0); r^2 < 1: a in [1, 2)
+    const bool big = e2 >= -63;
+    const uint64_t Ab = S + ((big && e2 <= 0) ? 1ull << ((-e2) & 63) : 0ull);
+    const bool cy = Ab < S;  // carry out of bit 63
+    const int ks = -e2 - 63;
+    const uint64_t As = 0x8000000000000000ull + (ks < 64 ? S >> (ks & 63) : 0ull);
+    const uint64_t A = big ? (cy ? (Ab >> 1) | 0x8000000000000000ull : Ab) : As;
+    ea = big ? e2 + 63 + (cy ? 1 : 0) : 0;
     float rf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)(uint32_t)(A >> 40)));
     const uint32_t fb = __float_as_uint(rf);
-    uint64_t Y = ((fb >> 23) & 0xFFu) >= 104u ? ~0ull
-                                              : (uint64_t)((fb & 0x7FFFFFu) | 0x800000u) << 40;
+    Y = ((fb >> 23) & 0xFFu) >= 104u ? ~0ull : (uint64_t)((fb & 0x7FFFFFu) | 0x800000u) << 40;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
         const uint64_t plo = A * Y, phi = __umul64hi(A, Y);
         const int64_t dh = (int64_t)(0x8000000000000000ull - phi - (plo != 0ull ? 1ull : 0ull));
         const uint64_t adh = dh < 0 ? (uint64_t)(-dh) : (uint64_t)dh;
         const uint64_t corr = __umul64hi(Y, adh << 1);  // Y |D| / 2^127
-        if (dh < 0) Y -= corr;
-        else Y = (Y + corr < Y) ? ~0ull : Y + corr;
+        const uint64_t ya = Y + corr;
+        Y = dh < 0 ? Y - corr : (ya < Y ? ~0ull : ya);
     }
-    // w = Y 2^(-64-ea): biased exponent E = 1022 - ea when normal
-    const int E = 1022 - ea;
-    if (E >= 1)
-        return pack_rn(0ull, E, Y >> 11, (Y >> 10) & 1ull, (Y & 0x3FFull) != 0ull ? 1ull : 0ull);
-    // subnormal: w = F 2^-1074 with F = Y 2^(E-12), rounded to nearest even
-    const int sh = 12 - E;  // >= 12
+}
+
+static __device__ __noinline__ double psi_weight_slow(double r)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(r);
+    const int er = (int)(b >> 52) & 0x7FF;
+    if (er == 0x7FF) return 1.0 / __fma_rn(r, r, 1.0);
+    uint64_t Y;
+    int ea;
+    psi_weight_core(b, er, Y, ea);
+    // subnormal w = F 2^-1074 with F = Y 2^(E-12), E = 1022 - ea < 1
+    const int sh = 12 - (1022 - ea);  // >= 12
     if (sh > 64) return 0.0;
     uint64_t F = sh == 64 ? 0ull : Y >> sh;
     const uint64_t rb = (Y >> (sh - 1)) & 1ull;
@@ -371,11 +377,24 @@ __device__ __forceinline__ double psi_weight_try(double r, bool& ok)
     return __longlong_as_double((long long)F);
 }
 
+__device__ __forceinline__ double psi_weight_try(double r, bool& ok)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(r);
+    const int er = (int)(b >> 52) & 0x7FF;
+    uint64_t Y;
+    int ea;
+    psi_weight_core(b, er, Y, ea);
+    const int E = 1022 - ea;  // biased exponent of w when normal
+    ok = er < 996 || (er != 0x7FF && E >= 1);
+    const double w = pack_rn(0ull, E, Y >> 11, (Y >> 10) & 1ull, (Y & 0x3FFull) != 0ull ? 1ull : 0ull);
+    return er < 996 ? 1.0 : w;
+}
+
 __device__ __forceinline__ double psi_weight(double r)
 {
     bool ok;
     const double w = psi_weight_try(r, ok);
-    return ok ? w : psi_weight_fp64(r);
+    return ok ? w : psi_weight_slow(r);
 }
 __device__ __forceinline__ float psi_weight(float r) { return rcp_(fma_(r, r, 1.0f)); }
 
@@ -397,15 +416,12 @@ template <typename T> struct PsiPrep {
     T r, r2, w;  // r, 2r, 1/(1 + r^2)
 };
 
-// In 3D the integer pipe already carries three 6-term neighbour sums, so
-// there the weight stays on the FP64 pipe (the rounded 1 + r^2 and the
-// refined reciprocal estimate); 1D and 2D take the integer-pipe psi_weight.
 template <typename T, int D> __device__ __forceinline__ PsiPrep<T> psi_prep(const Coef<T>& c, T u)
 {
     PsiPrep<T> pp;
     pp.r = fma_(-c.g, u, c.alpha);
     pp.r2 = twice(pp.r);
-    pp.w = D == 3 ? rcp_(fma_(pp.r, pp.r, T(1))) : psi_weight(pp.r);
+    pp.w = psi_weight(pp.r);
     return pp;
 }
 
@@ -424,11 +440,12 @@ __device__ __forceinline__ void psi_apply(const PsiPrep<T>& pp, T bSP, T bSQ, T&
 }
 
 // t' = (B SU + E |Psi|^2) / (1 + A s/2): the part of the (U,V) right side
-// fixed by the neighbours and the point's |Psi|^2.
-template <typename T> __device__ __forceinline__ T uv_src(const Coef<T>& c, T SU, T P, T Q)
+// fixed by the neighbours and the point's |Psi|^2, from BSU = B' SU (formed
+// once per point and pass with the neighbour sum: the red pass uses it twice).
+template <typename T> __device__ __forceinline__ T uv_src(const Coef<T>& c, T BSU, T P, T Q)
 {
     const T rho = fma_(P, P, mul_(Q, Q));
-    return fma_(c.Bp, SU, mul_(c.Ep, rho));
+    return fma_(c.Ep, rho, BSU);
 }
 
 // One (U,V) update, the implicit midpoint rule of the last two equations of
@@ -452,31 +469,31 @@ template <typename T> __device__ __forceinline__ void uv_step(const Coef<T>& c, 
 enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3 };
 
 // Update one point of the pass's colour in registers.  bSP, bSQ = beta S_P,
-// beta S_Q and SU = S_U from the neighbour sums above (neighbours are of the
-// other colour and fixed for the pass).
+// beta S_Q and BSU = B' S_U from the neighbour sums above (neighbours are of
+// the other colour and fixed for the pass).
 template <typename T, int D, int MODE>
-__device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T SU,
+__device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T BSU,
                                              T& P, T& Q, T& U, T& V)
 {
     if (MODE == RED_BASE) {
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
-        uv_step(c, uv_src(c, SU, P, Q), U, V);      // base (U,V) with |Psi^{n+1}|^2
+        uv_step(c, uv_src(c, BSU, P, Q), U, V);      // base (U,V) with |Psi^{n+1}|^2
     } else if (MODE == BLACK_FUSED) {
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // base Psi with U^n
         // base and adjoint (U,V): both use |Psi^{n+1}|^2 of the base half (the
         // adjoint's |Psi^n|^2) and the same neighbours
-        const T t = uv_src(c, SU, P, Q);
+        const T t = uv_src(c, BSU, P, Q);
         uv_step(c, t, U, V);
         uv_step(c, t, U, V);
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // adjoint Psi with U^{n+1}
     } else if (MODE == RED_FUSED) {
-        uv_step(c, uv_src(c, SU, P, Q), U, V);      // adjoint (U,V) with |Psi^n|^2
+        uv_step(c, uv_src(c, BSU, P, Q), U, V);      // adjoint (U,V) with |Psi^n|^2
         const PsiPrep<T> pp = psi_prep<T, D>(c, U);
         psi_apply(pp, bSP, bSQ, P, Q);              // adjoint Psi with U^{n+1}
         psi_apply(pp, bSP, bSQ, P, Q);              // next base Psi: same U, same r
-        uv_step(c, uv_src(c, SU, P, Q), U, V);      // next base (U,V)
+        uv_step(c, uv_src(c, BSU, P, Q), U, V);      // next base (U,V)
     } else {  // RED_ADJ
-        uv_step(c, uv_src(c, SU, P, Q), U, V);
+        uv_step(c, uv_src(c, BSU, P, Q), U, V);
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);
     }
 }

@@ -62,11 +62,11 @@ __device__ __forceinline__ int64_t colour_point(int64_t t, int64_t N, int parity
     return i;
 }
 
-// beta S_P, beta S_Q and S_U over the neighbours nb of colour_point.
+// beta S_P, beta S_Q and B' S_U over the neighbours nb of colour_point.
 template <typename T, int D, bool GLOBAL>
 __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t<T>* uv,
                                                const int64_t nb[2 * D], const Coef<T>& c,
-                                               T& bSP, T& bSQ, T& SU)
+                                               T& bSP, T& bSQ, T& BSU)
 {
     const T* u = reinterpret_cast<const T*>(uv);
     T p[2 * D], q[2 * D], w[2 * D];
@@ -79,7 +79,7 @@ __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t
     }
     bSP = nsum_scaled(p, c.beta);
     bSQ = nsum_scaled(q, c.beta);
-    SU = nsum(w);
+    BSU = nsum_scaled(w, c.Bp);
 }
 
 template <typename T, int D, int MODE, bool GLOBAL>
@@ -88,11 +88,11 @@ __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int6
 {
     int64_t nb[2 * D];
     const int64_t i = colour_point<D>(t, N, parity, nb);
-    T bSP, bSQ, SU;
-    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, c, bSP, bSQ, SU);
+    T bSP, bSQ, BSU;
+    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, c, bSP, bSQ, BSU);
     vec2_t<T> a = pq[i];
     vec2_t<T> b = uv[i];
-    update_point<T, D, MODE>(c, bSP, bSQ, SU, a.x, a.y, b.x, b.y);
+    update_point<T, D, MODE>(c, bSP, bSQ, BSU, a.x, a.y, b.x, b.y);
     pq[i] = a;
     uv[i] = b;
 }
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     }
     vec2_t<T> a = pq[i];
     vec2_t<T> b = uv[i];
-    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum(w), a.x, a.y, b.x, b.y);
+    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x, a.y, b.x, b.y);
     pq[i] = a;
     uv[i] = b;
 }

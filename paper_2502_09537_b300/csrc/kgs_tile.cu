@@ -92,7 +92,7 @@ __device__ __forceinline__ void tile_point(vec2_t<T>* spq, vec2_t<T>* suv, int o
     }
     vec2_t<T> a = spq[own];
     vec2_t<T> b = suv[own];
-    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum(w), a.x, a.y, b.x, b.y);
+    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x, a.y, b.x, b.y);
     spq[own] = a;
     suv[own] = b;
 }

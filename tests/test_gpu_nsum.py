@@ -67,6 +67,30 @@ def _expected_scaled(row, beta, exact):
     return beta * _expected(row, False)
 
 
+def _biased_exponent(x):
+    return (int(np.float64(x).view(np.uint64)) >> 52) & 0x7FF
+
+
+def _fast_path_expected(row):
+    """Whether the exact accumulator must take the row: finite values whose
+    nonzero members lie within 39 binades of the largest (a subnormal counts
+    as exponent 1), and an exact sum that is zero or has a normal exponent."""
+    if not all(math.isfinite(v) for v in row):
+        return False
+    es = [max(_biased_exponent(v), 1) for v in row]
+    nz = [e for e, v in zip(es, row) if v != 0.0]
+    if nz and max(es) - min(nz) > 39:
+        return False
+    f = sum(Fraction(v) for v in row)
+    if f == 0:
+        return True
+    a = abs(f)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if a < Fraction(2) ** e:
+        e -= 1
+    return 1 <= e + 1023 <= 0x7FE
+
+
 def _same(a, b):
     if math.isnan(a) and math.isnan(b):
         return True
@@ -86,8 +110,10 @@ def test_neighbour_sum_is_correctly_rounded(k, beta):
         if not _same(want, got[i]) or not _same(want2, scaled[i]):
             bad.append((row, want, float(got[i]), want2, float(scaled[i]), int(exact[i])))
     assert not bad, bad[:5]
-    # the exact path takes every row of finite normal values within 71 binades
-    assert (exact & 1).mean() > 0.7 and ((exact & 2) > 0).mean() > 0.6
+    # the exact path takes exactly the rows it should
+    want_fast = np.array([_fast_path_expected(r) for r in x.tolist()])
+    assert np.array_equal((exact & 1) == 1, want_fast)
+    assert want_fast.mean() > 0.6 and ((exact & 2) > 0).mean() > 0.55
 
 
 def test_neighbour_sum_fast_path_on_solver_like_values():
