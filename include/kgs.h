@@ -107,10 +107,52 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V,
                   int where, void* stream);
 
 /* Advance the state by nsteps >= 0 full DP-AVF2 steps of size tau (Eq. dp-comp
- * in the checkerboard order of Algorithm 3), asynchronously on stream.  On
- * completion the state is at a step boundary; kgs_step(a) then kgs_step(b)
- * gives bitwise the result of kgs_step(a + b). */
+ * in the checkerboard order of Algorithm 3, or the order set by
+ * kgs_set_order), asynchronously on stream.  On completion the state is at a
+ * step boundary; kgs_step(a) then kgs_step(b) gives bitwise the result of
+ * kgs_step(a + b). */
 int kgs_step(kgs_handle h, int64_t nsteps, void* stream);
+
+/* ---- update orders (Sec. 3, Eqs. LapP, order1, order2; Algorithms 1-2) ----
+ * Any order of the grid points defines a DP-AVF scheme: in a point's update
+ * the neighbours that come earlier in the order enter at the new level and
+ * the later ones at the old level (the S/W/E/N superscripts of Eq. LapP).
+ * DP-AVF2 visits the points in the order in its base half and in the reverse
+ * order in its adjoint half (Algorithm 1), in place.  The checkerboard of
+ * Algorithm 3 is the default; Eq. order1 is the lexicographic order (C order
+ * of the linear index), Algorithm 2 a block-splitting order.
+ *
+ * An order is a permutation of the linear indices 0 .. N^d - 1 of the grid
+ * (C order: index = (i0 N + i1) N + i2, last axis fastest).  It runs on the
+ * device as a level schedule: the level of a point is one more than the
+ * largest level of its neighbours that precede it in the order (0 if none);
+ * points of one level are never neighbours and are updated in parallel, the
+ * levels in increasing order in the base half and in decreasing order in the
+ * adjoint half.  This gives every point exactly the neighbour values of the
+ * serial order, so the result does not depend on how points of one level
+ * are ordered.  The checkerboard has 2 levels, the lexicographic order
+ * 1 + d (N - 1) (its anti-diagonal wavefronts).
+ *
+ * kgs_order_schedule: the levels of `order` (N^d int64, host, the caller's)
+ * written to level[0 .. N^d) (host, by linear index) and their count to
+ * *nlevels.  Host only: needs no device.  Returns KGS_OK, KGS_ERR_ARG (NULL
+ * argument, dim not 1-3, or order not a permutation), KGS_ERR_ODD_N,
+ * KGS_ERR_RANGE (N^d beyond what kgs_create takes) or KGS_ERR_OOM (host
+ * memory).
+ *
+ * kgs_set_order: make `order` (N^d int64, host; copied) the handle's update
+ * order from the next kgs_step on; NULL restores the checkerboard.  The
+ * handle keeps the points sorted by level on the device (8 bytes per point);
+ * the kernel options (KGS_OPT_*) apply to the checkerboard only.  Waits for
+ * the device to finish queued work first.  Returns KGS_OK, KGS_ERR_ARG (not
+ * a permutation; the handle's order is unchanged), KGS_ERR_OOM (host or
+ * device memory) or KGS_ERR_CUDA.
+ *
+ * kgs_order_levels: the number of levels of the handle's current order (2
+ * for the checkerboard). */
+int kgs_order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels);
+int kgs_set_order(kgs_handle h, const int64_t* order);
+int kgs_order_levels(kgs_handle h, int64_t* nlevels);
 
 /* Discrete invariants of the current state, computed on the device in float64
  * with compensated final summation, returned in host memory (synchronises

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/kgs.h"
 #include "kgs_internal.h"
@@ -62,6 +63,12 @@ struct kgs_solver {
     int graph_buf = -1;  // state buffer the graph was captured on
     Coef<double> cd{};
     Coef<float> cf{};
+    // update order other than the checkerboard (kgs_set_order): points sorted
+    // by level on the device, level offsets on the host; empty = checkerboard
+    int64_t* olist = nullptr;
+    std::vector<int64_t> olevels;
+    cudaGraphExec_t ograph = nullptr;  // one step of the order, captured
+    int ograph_buf = -1;
 };
 
 namespace {
@@ -110,6 +117,10 @@ void drop_graph(kgs_solver* h)
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
+    }
+    if (h->ograph) {
+        cudaGraphExecDestroy(h->ograph);
+        h->ograph = nullptr;
     }
 }
 
@@ -217,9 +228,81 @@ int ensure_graph(kgs_solver* h)
     return 0;
 }
 
+// One DP-AVF2 step in the handle's order: the base half over the levels in
+// increasing order, the adjoint half in decreasing order.
+template <typename T>
+int order_step(kgs_solver* h, cudaStream_t s)
+{
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    vec2_t<T>* pq = (vec2_t<T>*)h->pqb[h->cur];
+    vec2_t<T>* uv = (vec2_t<T>*)h->uvb[h->cur];
+    const int64_t nl = (int64_t)h->olevels.size() - 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t k = 0; k < nl; ++k) {
+            const int64_t l = pass == 0 ? k : nl - 1 - k;
+            const int64_t o = h->olevels[(size_t)l], n = h->olevels[(size_t)l + 1] - o;
+            const int r = launch_level<T>(h->dim, pass == 0 ? RED_BASE : RED_ADJ, pq, uv, h->olist + o, n,
+                                          h->N, *c, s);
+            if (r < 0) return -1;
+            h->launches += r;
+        }
+    }
+    return 0;
+}
+
+template <typename T>
+int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
+{
+    if (h->opt_graph && nsteps >= 2) {
+        if (!(h->ograph && h->ograph_buf == h->cur)) {
+            if (h->ograph) {
+                cudaGraphExecDestroy(h->ograph);
+                h->ograph = nullptr;
+            }
+            if (!h->capture_stream) {
+                cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+            }
+            cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+            const int64_t l0 = h->launches;
+            const int r = order_step<T>(h, h->capture_stream);
+            h->launches = l0;
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(h->capture_stream, &graph);
+            if (r < 0 && e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(h, e == cudaSuccess ? cudaErrorUnknown : e, "order step capture");
+            }
+            e = cudaGraphInstantiate(&h->ograph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                h->ograph = nullptr;
+                return cuda_fail(h, e, "cudaGraphInstantiate");
+            }
+            h->ograph_buf = h->cur;
+        }
+        int64_t per = 0;
+        for (size_t l = 0; l + 1 < h->olevels.size(); ++l) per += h->olevels[l + 1] > h->olevels[l];
+        for (int64_t k = 0; k < nsteps; ++k) {
+            cudaError_t e = cudaGraphLaunch(h->ograph, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            h->launches += 2 * per;
+        }
+        return KGS_OK;
+    }
+    for (int64_t k = 0; k < nsteps; ++k)
+        if (order_step<T>(h, s)) return cuda_fail(h, cudaGetLastError(), "order level launch");
+    return KGS_OK;
+}
+
 template <typename T>
 int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 {
+    if (!h->olevels.empty()) return step_in_order<T>(h, nsteps, s);
     const Coef<T>* c;
     if constexpr (sizeof(T) == 8) c = &h->cd;
     else c = &h->cf;
@@ -279,6 +362,8 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 void free_all(kgs_solver* h)
 {
     drop_graph(h);
+    cudaFree(h->olist);
+    h->olist = nullptr;
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->pqb[b]);
@@ -457,6 +542,63 @@ int kgs_step(kgs_handle h, int64_t nsteps, void* stream)
     if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
     return h->precision == 64 ? step_impl<double>(h, nsteps, (cudaStream_t)stream)
                               : step_impl<float>(h, nsteps, (cudaStream_t)stream);
+}
+
+int kgs_order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels)
+{
+    g_last_status = KGS_OK;
+    if (dim < 1 || dim > 3) return fail(KGS_ERR_ARG, "dim must be 1, 2 or 3 (got %d)", dim);
+    if (N < 4 || (N & 1)) return fail(KGS_ERR_ODD_N, "N must be even and >= 4 (got %lld)", (long long)N);
+    if ((dim == 3 && N > 4096) || (dim == 2 && N > 65534) || N > ((int64_t)1 << 30))
+        return fail(KGS_ERR_RANGE, "N^d too large");
+    if (!order || !level || !nlevels) return fail(KGS_ERR_ARG, "NULL argument");
+    const int st = order_schedule(dim, N, order, level, nlevels);
+    if (st == -3) return fail(KGS_ERR_OOM, "host memory for the order schedule");
+    if (st) return fail(KGS_ERR_ARG, "order is not a permutation of 0 .. N^d - 1");
+    return KGS_OK;
+}
+
+int kgs_set_order(kgs_handle h, const int64_t* order)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+    // the previous order's list may still be read by queued work
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+    drop_graph(h);
+    if (!order) {
+        cudaFree(h->olist);
+        h->olist = nullptr;
+        h->olevels.clear();
+        return KGS_OK;
+    }
+    std::vector<int64_t> list, off;
+    st = order_lists(h->dim, h->N, order, list, off);
+    if (st == -3) return fail(KGS_ERR_OOM, "host memory for the order schedule");
+    if (st) return fail(KGS_ERR_ARG, "order is not a permutation of 0 .. N^d - 1");
+    if (!h->olist) {
+        e = cudaMalloc(&h->olist, (size_t)h->M * sizeof(int64_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->olist = nullptr;
+            return fail(KGS_ERR_OOM, "device memory for the order (%lld points)", (long long)h->M);
+        }
+    }
+    e = cudaMemcpy(h->olist, list.data(), (size_t)h->M * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "order upload");
+    h->olevels.swap(off);
+    return KGS_OK;
+}
+
+int kgs_order_levels(kgs_handle h, int64_t* nlevels)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (!nlevels) return fail(KGS_ERR_ARG, "NULL output");
+    *nlevels = h->olevels.empty() ? 2 : (int64_t)h->olevels.size() - 1;
+    return KGS_OK;
 }
 
 int kgs_invariants(kgs_handle h, double* out3, void* stream)

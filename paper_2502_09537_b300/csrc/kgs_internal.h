@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "kgs_point.cuh"
 
 namespace kgs {
@@ -47,6 +49,19 @@ int64_t tile_smem_bytes(int dim, int elem_bytes, const TileParams& tp);
 template <typename T>
 int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<T>* uv,
                 vec2_t<T>* pq_out, vec2_t<T>* uv_out, const Coef<T>& c, cudaStream_t stream);
+
+// Update orders (kgs_order.cu).  order_schedule: level of every point of a
+// permutation `order` of the N^dim grid (returns 0, -1 if order is not a
+// permutation, -3 if host memory ran out).  order_lists: the points sorted by
+// level (stable in order position) and the level offsets (nlevels + 1).
+// launch_level: one level's points, MODE RED_BASE (base half) or RED_ADJ
+// (adjoint half); returns 1, 0 for an empty level, -1 if the launch failed.
+int order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels);
+int order_lists(int dim, int64_t N, const int64_t* order, std::vector<int64_t>& list,
+                std::vector<int64_t>& offsets);
+template <typename T>
+int launch_level(int dim, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t* list, int64_t count,
+                 int64_t N, const Coef<T>& c, cudaStream_t s);
 
 // Layout conversion (kgs_layout.cu): one float64 field <-> one component of a vec2 array.
 template <typename T>

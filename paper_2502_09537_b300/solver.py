@@ -51,6 +51,9 @@ SIGNATURES = {
     "kgs_set_option": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64]),
     "kgs_launch_count": (_c_int64, [_vp]),
     "kgs_destroy": (None, [_vp]),
+    "kgs_order_schedule": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _vp, ctypes.POINTER(_c_int64)]),
+    "kgs_set_order": (ctypes.c_int, [_vp, _vp]),
+    "kgs_order_levels": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64)]),
     "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kgs_last_error": (ctypes.c_char_p, []),
     "kgs_last_status": (ctypes.c_int, []),
@@ -197,6 +200,22 @@ class Solver:
     def set_option(self, option: int, value: int):
         _check(self._lib.kgs_set_option(self._h, int(option), int(value)))
 
+    def set_order(self, order=None):
+        """Update order of the following steps: a permutation of the linear
+        indices 0 .. N^d - 1 (visited in this order by the base half, in the
+        reverse order by the adjoint half), or None for the checkerboard."""
+        if order is None:
+            _check(self._lib.kgs_set_order(self._h, None))
+            return
+        o = _order_array(order, self.N ** self.dim)
+        _check(self._lib.kgs_set_order(self._h, o.ctypes.data))
+
+    def order_levels(self) -> int:
+        """Parallel levels per half step of the current order (2 for the checkerboard)."""
+        n = ctypes.c_int64()
+        _check(self._lib.kgs_order_levels(self._h, ctypes.byref(n)))
+        return n.value
+
     # diagnostics ---------------------------------------------------------
     def invariants(self, stream=None):
         """(E_h, S_E, mass) in float64."""
@@ -217,6 +236,24 @@ class Solver:
     @property
     def launch_count(self) -> int:
         return int(self._lib.kgs_launch_count(self._h))
+
+
+def _order_array(order, M: int) -> np.ndarray:
+    o = np.ascontiguousarray(order, dtype=np.int64).ravel()
+    if o.size != M:
+        raise ValueError(f"an order has N^d = {M} entries (got {o.size})")
+    return o
+
+
+def order_schedule(dim: int, N: int, order):
+    """(level of every point by linear index, number of levels) of an update
+    order, computed by the library on the host (kgs_order_schedule)."""
+    lib = load_library()
+    o = _order_array(order, N ** dim)
+    level = np.empty(o.size, dtype=np.int32)
+    n = ctypes.c_int64()
+    _check(lib.kgs_order_schedule(int(dim), int(N), o.ctypes.data, level.ctypes.data, ctypes.byref(n)))
+    return level.reshape((N,) * dim), n.value
 
 
 def probe_fma_rate(precision: int = 64, iters: int = 4096, blocks_per_sm: int = 8, stream=None):

@@ -1,0 +1,129 @@
+"""General update orders on the GPU (Sec. 3; Algorithms 1-3) against the oracle.
+
+kgs_set_order runs any order of the points as a level schedule.  Checked
+here: the checkerboard given as an order is bitwise the fused colour passes
+(same pointwise arithmetic, same neighbour values); orders with the same
+levels are bitwise equal; the lexicographic order (Eq. order1), its reverse
+(Eq. order2), Algorithm 2's block order, the black-first checkerboard and
+random orders match the oracle's serial DP-AVF2 in that order (float64 bar
+1e-12, as for the checkerboard); energy is conserved in the lexicographic
+order; the order can be reset and bad orders are rejected.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2502_09537_b300 import orders  # noqa: E402
+from paper_2502_09537_b300.inputs import Problem, random_state  # noqa: E402
+from paper_2502_09537_b300.solver import (KGS_FP32, KGS_FP64, KGS_OPT_GRAPH, KGSError,  # noqa: E402
+                                          Solver, order_schedule)
+
+FP64_BAR = 1e-12
+
+
+def _copy(st):
+    return tuple(np.array(a, dtype=np.float64, copy=True) for a in st)
+
+
+def _gpu(prob, st, order, splits, precision=KGS_FP64, graph=1):
+    with Solver.from_problem(prob, precision) as s:
+        s.set_option(KGS_OPT_GRAPH, graph)
+        s.set_state(*_copy(st))
+        if order is not None:
+            s.set_order(order)
+        for n in splits:
+            s.step(n)
+        return s.get_state(), s.order_levels()
+
+
+def _rel(a, b):
+    return max(np.abs(x - y).max() / max(np.abs(y).max(), 1e-300) for x, y in zip(a, b))
+
+
+def _bitwise(a, b):
+    return all(np.array_equal(x.view(np.uint64), y.view(np.uint64)) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+@pytest.mark.parametrize("dim,N", [(1, 64), (2, 32), (3, 10)])
+def test_checkerboard_as_an_order_is_the_colour_passes(dim, N, precision):
+    prob = Problem(dim, N, 8.0, 1.0, 0.8, 1.2, 0.9, 0.02)
+    st = random_state(prob, 2502_09537 + 60 + dim)
+    ref, lv0 = _gpu(prob, st, None, [7], precision)
+    got, lv = _gpu(prob, st, orders.checkerboard(dim, N), [7], precision)
+    assert lv0 == 2 and lv == 2
+    assert _bitwise(got, ref)
+    # the same levels in another order within each level
+    perm = orders.checkerboard(dim, N)
+    red = perm[: N ** dim // 2][::-1]
+    black = perm[N ** dim // 2:][::-1]
+    got2, _ = _gpu(prob, st, np.concatenate([red, black]), [3, 4], precision, graph=0)
+    assert _bitwise(got2, ref)
+
+
+@pytest.mark.parametrize("name,dim,N,nsteps", [
+    ("lexicographic", 1, 64, 40),
+    ("lexicographic", 2, 24, 60),
+    ("reverse_lexicographic", 2, 20, 60),
+    ("lexicographic", 3, 8, 30),
+    ("black_first", 2, 16, 50),
+    ("block_split", 2, 26, 40),
+    ("random", 2, 12, 40),
+    ("random", 3, 6, 20),
+])
+def test_order_matches_oracle(orc, name, dim, N, nsteps):
+    prob = Problem(dim, N, 10.0, 1.0, 0.8, 1.1, 0.9, 0.01)
+    st = random_state(prob, 2502_09537 + 70 + N)
+    if name == "lexicographic":
+        order = orders.lexicographic(dim, N)
+    elif name == "reverse_lexicographic":
+        order = orders.reverse_lexicographic(dim, N)
+    elif name == "black_first":
+        order = orders.checkerboard(dim, N, red_first=False)
+    elif name == "block_split":
+        order = orders.block_split_2d(N, 4)
+    else:
+        order = orders.random_order(dim, N, 2502_09537 + 80 + N)
+    want = _copy(st)
+    orc.steps_order(prob, *want, order, nsteps)
+    got, lv = _gpu(prob, st, order, [nsteps])
+    assert lv == order_schedule(dim, N, order)[1]
+    assert _rel(got, want) <= FP64_BAR, _rel(got, want)
+    # split calls (graph replays vs direct launches) give bitwise the same state
+    got2, _ = _gpu(prob, st, order, [1, nsteps - 1], graph=0)
+    assert _bitwise(got, got2)
+
+
+def test_energy_conserved_in_lexicographic_order(orc):
+    prob = Problem(2, 32, 16.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 90)
+    with Solver.from_problem(prob) as s:
+        s.set_state(*_copy(st))
+        s.set_order(orders.lexicographic(2, 32))
+        E0, S0, _ = s.invariants()
+        s.step(2000)
+        E1, S1, _ = s.invariants()
+    assert abs(E1 - E0) / max(S0, S1) < 1e-13
+
+
+def test_reset_and_bad_orders():
+    prob = Problem(2, 16, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 91)
+    ref, _ = _gpu(prob, st, None, [5])
+    with Solver.from_problem(prob) as s:
+        s.set_state(*_copy(st))
+        s.set_order(orders.lexicographic(2, 16))
+        assert s.order_levels() == 31
+        bad = orders.lexicographic(2, 16)
+        bad[0] = 1
+        with pytest.raises(KGSError):
+            s.set_order(bad)
+        assert s.order_levels() == 31          # unchanged by the rejected order
+        s.set_order(None)
+        assert s.order_levels() == 2
+        s.step(5)
+        assert _bitwise(s.get_state(), ref)
