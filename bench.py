@@ -35,6 +35,13 @@ UNIT = "point-updates/s"
 ENERGY_EVERY = 100
 
 
+def flops_per_point_update_unfused(dim: int) -> float:
+    """FP64-pipe flops of one point-update in a general order (kgs_set_order):
+    no fusion, every point takes one base update (prepare 2, apply 12, source
+    5, step 7) and one adjoint update per step: 2 x 26 = 52."""
+    return 2 * (2 + 12 + 5 + 7)
+
+
 def flops_per_point_update(dim: int) -> float:
     """FP64-pipe flops of one point-update (one point, one full DP-AVF2 step)
     as the FP64 colour passes execute them (kgs_point.cuh), FMA = 2, add/mul
@@ -61,7 +68,8 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 # DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
 # ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
 # the kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("3d", "fp32"): 2.156e9 + 2.091e9}     # pass_kernel_fp32_kgs3d_N512.md
+NCU_TRAFFIC = {("2d", "fp64"): 134.38e6 + 74.17e6,   # pass_kernel_fp64_kgs2d_N2048.md
+               ("3d", "fp32"): 2.156e9 + 2.091e9}     # pass_kernel_fp32_kgs3d_N512.md
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), 148 SMs, 2032 MHz maximum SM
@@ -75,14 +83,15 @@ def bytes_per_point_update(elem: int) -> int:
     return 2 * 4 * elem
 
 
-def make_workload(name: str):
+def make_workload(name: str, n: int = 0):
+    """The benchmark configuration; n overrides the points per direction."""
     from paper_2502_09537_b300 import inputs
     if name == "2d":
-        return inputs.gauss_2d(2048, 1000)
+        return inputs.gauss_2d(n or 2048, 1000)
     if name == "1d":
-        return inputs.soliton_1d(512, 2000)
+        return inputs.soliton_1d(n or 512, 2000)
     if name == "3d":
-        return inputs.gauss_3d(512, 200)
+        return inputs.gauss_3d(n or 512, 200)
     raise ValueError(name)
 
 
@@ -430,6 +439,13 @@ def main():
     ap.add_argument("--kernel", type=int, default=0,
                     help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
+    ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block"],
+                    help="update order: the checkerboard (Algorithm 3), the lexicographic "
+                         "wavefront (Eq. order1) or Algorithm 2's block order (2D, 16 blocks)")
+    ap.add_argument("--steps-per-solve", type=int, default=0,
+                    help="DP-AVF2 steps per benchmark step (default: the workload's)")
+    ap.add_argument("--grid-n", type=int, default=0,
+                    help="points per direction instead of the workload's (small cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -455,7 +471,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    work = make_workload(args.workload)
+    work = make_workload(args.workload, args.grid_n)
+    if args.steps_per_solve:
+        work = work._replace(nsteps=args.steps_per_solve)
     prob = work.prob
     precision = KGS_FP64 if args.precision == "fp64" else KGS_FP32
     elem = 8 if precision == KGS_FP64 else 4
@@ -472,6 +490,10 @@ def main():
         s.set_option(KGS_OPT_KERNEL, args.kernel)
     if args.ppt:
         s.set_option(KGS_OPT_PPT, args.ppt)
+    if args.order != "checkerboard":
+        from paper_2502_09537_b300 import orders
+        s.set_order(orders.lexicographic(prob.dim, prob.N) if args.order == "lex"
+                    else orders.block_split_2d(prob.N, 16))
     torch.cuda.synchronize()
 
     with torch.cuda.stream(stream):
@@ -528,16 +550,19 @@ def main():
     peaks = measured_peaks()
     if precision == KGS_FP64:
         fma_rate, _ = probe_fma_rate(64, 2048, 8, stream)
-        flops_per_launch = upd_per_launch * flops_per_point_update(prob.dim)
+        fpu = (flops_per_point_update(prob.dim) if args.order == "checkerboard"
+               else flops_per_point_update_unfused(prob.dim))
+        flops_per_launch = upd_per_launch * fpu
         achieved = flops_per_launch / (pass_ms * 1e-3) / 1e12
         peak = FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+                "traffic": (NCU_TRAFFIC.get((args.workload, args.precision))
+                            if args.order == "checkerboard" else None),
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
                 "probe_tflops": 2 * fma_rate / 1e12,
                 "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r and 1/(1+r^2) run on the integer pipes)",
-                "flops_per_point_update": flops_per_point_update(prob.dim),
+                "flops_per_point_update": fpu,
                 "algorithmic_flops_per_point_update": algorithmic_flops_per_point_update(prob.dim),
                 "algorithmic_tflops": upd_per_launch * algorithmic_flops_per_point_update(prob.dim)
                 / (pass_ms * 1e-3) / 1e12,
@@ -558,7 +583,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
-                   "threads": args.threads or 256, "kernel": args.kernel,
+                   "threads": args.threads or 256, "kernel": args.kernel, "order": args.order,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",
