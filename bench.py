@@ -437,7 +437,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
     ap.add_argument("--kernel", type=int, default=0,
-                    help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent")
+                    help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent, "
+                         "5 slab-pipelined passes")
+    ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab kernel)")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
     ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block"],
                     help="update order: the checkerboard (Algorithm 3), the lexicographic "
@@ -490,6 +492,9 @@ def main():
         s.set_option(KGS_OPT_KERNEL, args.kernel)
     if args.ppt:
         s.set_option(KGS_OPT_PPT, args.ppt)
+    if args.slab_planes:
+        from paper_2502_09537_b300.solver import KGS_OPT_SLAB_PLANES
+        s.set_option(KGS_OPT_SLAB_PLANES, args.slab_planes)
     if args.order != "checkerboard":
         from paper_2502_09537_b300 import orders
         s.set_order(orders.lexicographic(prob.dim, prob.N) if args.order == "lex"
@@ -584,6 +589,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
                    "threads": args.threads or 256, "kernel": args.kernel, "order": args.order,
+                   "slab_planes": args.slab_planes,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",

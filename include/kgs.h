@@ -65,7 +65,8 @@ extern "C" {
 #define KGS_OPT_KERNEL   1  /* 0 auto, 1 one launch per colour pass, 2 shared-memory resident,
                                3 temporally blocked tiles (dim 2, 3; allocates a second state
                                buffer of the same size on first use), 4 persistent grid-stride
-                               colour passes */
+                               colour passes, 5 colour passes pipelined in axis-0 slabs through
+                               L2 (dim 2, 3; see KGS_OPT_SLAB_PLANES) */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
 #define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
 #define KGS_OPT_PPT      4  /* points of one colour per thread in those kernels: 1 only (2 was
@@ -75,6 +76,12 @@ extern "C" {
 #define KGS_OPT_TILE_LX      7  /* tile kernel: axis-0 planes per CTA */
 #define KGS_OPT_TILE_PASSES  8  /* tile kernel: colour passes per launch (= halo width), 1..8 */
 #define KGS_OPT_TILE_THREADS 9  /* tile kernel: threads per CTA (64, 128, 256, 512, 1024) */
+#define KGS_OPT_SLAB_PLANES 10  /* slab kernel: axis-0 planes per slab, 1 .. N; 0 (default) picks
+                                   about a quarter of the L2 cache's bytes per slab.  A step's
+                                   black pass runs slab by slab and each slab's red pass follows
+                                   the next slab's black pass, so the two passes reuse the state
+                                   in L2 instead of reading it from HBM twice; every point sees
+                                   the neighbour values of the two full passes (bitwise equal) */
 
 typedef struct kgs_solver* kgs_handle;
 

@@ -54,6 +54,7 @@ struct kgs_solver {
     bool state_set = false;
     int sticky = 0;  // first CUDA error seen (cudaError_t), 0 if none
     int opt_kernel = 0, opt_graph = 1, opt_threads = 256;
+    int64_t opt_slab = 0;  // planes per slab of the slab kernel (0: from the L2 size)
     TileParams tile{};
     bool tile_set = false;  // tile parameters chosen by the caller
     cudaStream_t last_stream = nullptr;
@@ -61,6 +62,7 @@ struct kgs_solver {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_buf = -1;  // state buffer the graph was captured on
+    int64_t graph_launches = 0;  // kernels per replay of the graph
     Coef<double> cd{};
     Coef<float> cf{};
     // update order other than the checkerboard (kgs_set_order): points sorted
@@ -134,7 +136,7 @@ Grid grid_of(const kgs_solver* h)
     return g;
 }
 
-enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4 };
+enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5 };
 
 // Default tile shape per dimension and precision (measured on B300; the batch
 // autotuner can override it per handle).
@@ -154,7 +156,7 @@ TileParams default_tile(int dim, int precision)
 int kernel_choice(const kgs_solver* h)
 {
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
-    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_PERSIST) return h->opt_kernel;
+    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_SLAB) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
     // Measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass beats the
     // temporally blocked tiles in both precisions (FP32: 8.6e10 vs 6.2e10 /
@@ -195,6 +197,60 @@ int pass(kgs_solver* h, int mode, cudaStream_t s)
     return 0;
 }
 
+// Planes per slab: the caller's choice, else about a quarter of L2 per slab.
+int64_t slab_planes(const kgs_solver* h)
+{
+    if (h->opt_slab > 0) return h->opt_slab < h->N ? h->opt_slab : h->N;
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) != cudaSuccess || l2 <= 0)
+        l2 = 126 << 20;
+    const int64_t plane = h->M / h->N * 2 * (h->precision == 64 ? 16 : 8);
+    int64_t p = (int64_t)(l2 / 4) / plane;
+    if (p < 2) p = 2;
+    return p < h->N ? p : h->N;
+}
+
+// One (BLACK_FUSED, red) pair of colour passes, red = RED_FUSED or RED_ADJ.
+// With the slab kernel the black pass runs slab by slab along axis 0 and the
+// red pass of slab s - 1 follows the black pass of slab s: the red pass of a
+// plane needs the black planes on both sides updated, and the black pass of a
+// plane needs the red planes on both sides not yet updated, so red plane 0
+// (whose lower neighbour is black plane N - 1, by periodicity) goes last.
+template <typename T>
+int pass_pair(kgs_solver* h, int red, cudaStream_t s)
+{
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    vec2_t<T>* pq = (vec2_t<T>*)h->pqb[h->cur];
+    vec2_t<T>* uv = (vec2_t<T>*)h->uvb[h->cur];
+    Grid g = grid_of(h);
+    if (kernel_choice(h) != K_SLAB || h->dim < 2) {
+        if (launch_pass<T>(g, BLACK_FUSED, pq, uv, *c, s) < 0 || launch_pass<T>(g, red, pq, uv, *c, s) < 0)
+            return -1;
+        h->launches += 2;
+        return 0;
+    }
+    const int64_t S = slab_planes(h), N = h->N;
+    const int64_t ns = (N + S - 1) / S;
+    auto run = [&](int mode, int64_t p0, int64_t p1) -> int {
+        if (p1 <= p0) return 0;
+        g.plane0 = p0;
+        g.planes = p1 - p0;
+        if (launch_pass<T>(g, mode, pq, uv, *c, s) < 0) return -1;
+        h->launches += 1;
+        return 0;
+    };
+    auto end = [&](int64_t k) { return (k + 1) * S < N ? (k + 1) * S : N; };
+    if (run(BLACK_FUSED, 0, end(0))) return -1;
+    for (int64_t k = 1; k < ns; ++k) {
+        if (run(BLACK_FUSED, k * S, end(k))) return -1;
+        if (run(red, k == 1 ? 1 : (k - 1) * S, end(k - 1))) return -1;
+    }
+    if (run(red, ns == 1 ? 1 : (ns - 1) * S, N)) return -1;
+    return run(red, 0, 1);
+}
+
 template <typename T>
 int ensure_graph(kgs_solver* h)
 {
@@ -209,14 +265,17 @@ int ensure_graph(kgs_solver* h)
     const Coef<T>* c;
     if constexpr (sizeof(T) == 8) c = &h->cd;
     else c = &h->cf;
-    for (int k = 0; k < kGraphPairs; ++k) {
-        launch_pass<T>(grid_of(h), BLACK_FUSED, (vec2_t<T>*)h->pqb[h->cur],
-                       (vec2_t<T>*)h->uvb[h->cur], *c, h->capture_stream);
-        launch_pass<T>(grid_of(h), RED_FUSED, (vec2_t<T>*)h->pqb[h->cur],
-                       (vec2_t<T>*)h->uvb[h->cur], *c, h->capture_stream);
-    }
+    const int64_t l0 = h->launches;
+    int bad = 0;
+    for (int k = 0; k < kGraphPairs && !bad; ++k) bad = pass_pair<T>(h, RED_FUSED, h->capture_stream);
+    h->graph_launches = h->launches - l0;
+    h->launches = l0;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (bad && e == cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, cudaErrorLaunchFailure, "colour pass capture");
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&h->graph, graph, 0);
     cudaGraphDestroy(graph);
@@ -346,16 +405,14 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
         while (pairs >= kGraphPairs) {
             cudaError_t e = cudaGraphLaunch(h->graph, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
-            h->launches += 2 * kGraphPairs;
+            h->launches += h->graph_launches;
             pairs -= kGraphPairs;
         }
     }
     for (; pairs > 0; --pairs) {
-        if (pass<T>(h, BLACK_FUSED, s) || pass<T>(h, RED_FUSED, s))
-            return cuda_fail(h, cudaGetLastError(), "colour pass launch");
+        if (pass_pair<T>(h, RED_FUSED, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
     }
-    if (pass<T>(h, BLACK_FUSED, s) || pass<T>(h, RED_ADJ, s))
-        return cuda_fail(h, cudaGetLastError(), "colour pass launch");
+    if (pass_pair<T>(h, RED_ADJ, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
     return KGS_OK;
 }
 
@@ -669,7 +726,8 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     if (st) return st;
     switch (option) {
     case KGS_OPT_KERNEL:
-        if (value < 0 || value > 4) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 4");
+        if (value < 0 || value > 5) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 5");
+        if (value == 5 && h->dim < 2) return fail(KGS_ERR_ARG, "the slab kernel needs dim 2 or 3");
         if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))
             return fail(KGS_ERR_RANGE, "grid too large for the shared-memory resident kernel");
         if (value == 3 && h->dim < 2)
@@ -708,6 +766,11 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     case KGS_OPT_GRAPH:
         if (value < 0 || value > 1) return fail(KGS_ERR_ARG, "KGS_OPT_GRAPH takes 0 or 1");
         h->opt_graph = (int)value;
+        return KGS_OK;
+    case KGS_OPT_SLAB_PLANES:
+        if (value < 0 || value > h->N) return fail(KGS_ERR_ARG, "KGS_OPT_SLAB_PLANES takes 0 to N");
+        h->opt_slab = value;
+        drop_graph(h);
         return KGS_OK;
     case KGS_OPT_THREADS:
         if (value != 128 && value != 256 && value != 512)

@@ -17,6 +17,9 @@ struct Grid {
     int64_t M;
     int threads = 256;  // CTA size of the colour-pass kernels (128, 256 or 512)
     bool persistent = false;  // grid-stride persistent colour passes
+    // axis-0 planes a colour pass covers: [plane0, plane0 + planes); planes = 0
+    // means all N (one-launch-per-pass kernels only; 2D and 3D)
+    int64_t plane0 = 0, planes = 0;
 };
 
 // Largest point count the shared-memory resident kernel takes for state type T

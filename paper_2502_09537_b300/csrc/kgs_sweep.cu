@@ -103,7 +103,7 @@ __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int6
 // N/2 points of the pass's colour in the row.  32-bit indices when N^d < 2^31.
 template <typename T, int D, int MODE, typename I>
 __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c,
-                                                   int parity)
+                                                   int parity, int plane0)
 {
     const int kk = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * kk >= N) return;
@@ -111,11 +111,11 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     int i0 = 0, i1 = 0, rp = 0;
     I row = 0;
     if (D == 2) {
-        i0 = blockIdx.y;
+        i0 = plane0 + (int)blockIdx.y;
         rp = i0 & 1;
         row = i0;
     } else if (D == 3) {
-        i0 = blockIdx.z;
+        i0 = plane0 + (int)blockIdx.z;
         i1 = blockIdx.y;
         rp = (i0 + i1) & 1;
         row = (I)i0 * n + i1;
@@ -222,13 +222,15 @@ static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coe
     const int hN = (int)(g.N >> 1);
     int threads = g.threads > 0 ? g.threads : 256;
     if (threads > hN) threads = (hN + 31) / 32 * 32;  // short rows: no idle warps
-    dim3 grid((unsigned)((hN + threads - 1) / threads), D >= 2 ? (unsigned)g.N : 1u,
-              D == 3 ? (unsigned)g.N : 1u);
+    const int64_t planes = (D >= 2 && g.planes > 0) ? g.planes : g.N;
+    const int plane0 = D >= 2 ? (int)g.plane0 : 0;
+    dim3 grid((unsigned)((hN + threads - 1) / threads), D == 2 ? (unsigned)planes : (D == 3 ? (unsigned)g.N : 1u),
+              D == 3 ? (unsigned)planes : 1u);
     const int parity = (MODE == BLACK_FUSED) ? (red_parity(D) ^ 1) : red_parity(D);
     if (g.M < ((int64_t)1 << 31))
-        pass_kernel<T, D, MODE, int32_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity);
+        pass_kernel<T, D, MODE, int32_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0);
     else
-        pass_kernel<T, D, MODE, int64_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity);
+        pass_kernel<T, D, MODE, int64_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0);
 }
 
 // CTAs for the persistent pass: 148 SMs x b CTAs of 256 threads, b in 3..6

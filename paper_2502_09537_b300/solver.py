@@ -32,6 +32,7 @@ KGS_OPT_TILE_T2 = 6
 KGS_OPT_TILE_LX = 7
 KGS_OPT_TILE_PASSES = 8
 KGS_OPT_TILE_THREADS = 9
+KGS_OPT_SLAB_PLANES = 10
 
 # Every function the header declares, with its ctypes signature.
 _c_int64 = ctypes.c_int64

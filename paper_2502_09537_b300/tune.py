@@ -5,7 +5,8 @@ precision) -- it times every candidate launch shape on a representative
 problem of that bucket and keeps the fastest:
 
   * the colour-pass kernel (one launch per pass) with 128, 256 or 512 threads
-    per CTA, and its persistent grid-stride variant;
+    per CTA, its persistent grid-stride variant and its slab-pipelined
+    schedule (2D, 3D);
   * the temporally blocked tile kernel with a few tile shapes (tile extents,
     passes per launch, threads per CTA) that fit in shared memory;
   * the shared-memory resident kernel, when the grid fits in one CTA.
@@ -49,6 +50,8 @@ def candidates(prob, precision: int) -> List[Options]:
     elem = 8 if precision == KGS_FP64 else 4
     out: List[Options] = [{KGS_OPT_KERNEL: 1, KGS_OPT_THREADS: t} for t in (128, 256, 512)]
     out.append({KGS_OPT_KERNEL: 4})  # persistent grid-stride passes
+    if prob.dim >= 2:
+        out.append({KGS_OPT_KERNEL: 5})  # colour passes pipelined in L2-sized axis-0 slabs
     if prob.points <= SMEM_BYTES // (4 * elem):
         out.append({KGS_OPT_KERNEL: 2})
     if prob.dim == 2:

@@ -106,8 +106,35 @@ def test_kernel_variants_and_graphs_are_bitwise_equal():
     b = run_gpu(prob, st, 100, kernel=1, graph=0)
     c = run_gpu(prob, st, 100, kernel=2)
     d = run_gpu(prob, st, 100, kernel=4)
-    for x, y, z, q in zip(a, b, c, d):
-        assert np.array_equal(x, y) and np.array_equal(x, z) and np.array_equal(x, q)
+    e = run_gpu(prob, st, 100, kernel=5)
+    for x, y, z, q, r in zip(a, b, c, d, e):
+        assert (np.array_equal(x, y) and np.array_equal(x, z) and np.array_equal(x, q)
+                and np.array_equal(x, r))
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+@pytest.mark.parametrize("dim,N,planes", [(2, 40, 1), (2, 40, 3), (2, 40, 7), (2, 40, 40),
+                                          (3, 12, 1), (3, 12, 2), (3, 12, 5), (3, 12, 0)])
+def test_slab_pipelined_passes_are_bitwise_the_full_passes(dim, N, planes, precision):
+    """The slab kernel (KGS_OPT_KERNEL = 5) reorders the launches of each
+    (black, red) pass pair along axis 0; every point still sees the neighbour
+    values of the two full passes, so the state is bitwise the same for any
+    slab size (a ragged last slab and the wrap-around plane included)."""
+    from paper_2502_09537_b300.solver import KGS_OPT_SLAB_PLANES
+    prob = Problem(dim, N, 9.0, 1.0, 0.9, 1.1, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 95 + planes, 0.5)
+    ref = run_gpu(prob, st, 45, precision=precision, kernel=1)
+    for graph in (1, 0):
+        with Solver.from_problem(prob, precision) as s:
+            s.set_option(KGS_OPT_KERNEL, 5)
+            s.set_option(KGS_OPT_SLAB_PLANES, planes)
+            s.set_option(KGS_OPT_GRAPH, graph)
+            s.set_state(*copy_state(st))
+            s.step(5)
+            s.step(40)
+            got = s.get_state()
+        for x, y in zip(ref, got):
+            assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("dim,N", [(2, 66), (3, 18), (1, 2050)])
@@ -130,7 +157,7 @@ def test_launch_shapes_are_bitwise_equal(dim, N, threads, ppt):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5])
 def test_split_steps_are_bitwise_equal(kernel):
     """kgs_step(a); kgs_step(b) == kgs_step(a+b), across graph boundaries too."""
     prob = Problem(2, 48, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
