@@ -8,11 +8,13 @@
 // admit new instances as others finish.
 //
 // Stepping: a DP-AVF2 step of every instance is two colour passes (kgs_point.cuh:
-// RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ).  One launch
-// per precision applies one pass to all instances: a persistent grid of CTAs
-// walks a work list of 256-point chunks of every instance's points of that
-// colour.  Each instance i may run its own number of steps n_i; launch g
-// applies pass g of an instance's run while g <= 2 n_i and skips it after.  The
+// RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ).  Pass g of
+// every instance is applied by a persistent grid of CTAs walking a work list of
+// 256-point chunks of the instances' points of that colour, one launch per
+// precision, dimension and pass mode that occurs at pass g (each kernel is
+// specialised on them); a chunk's instance is read from a table built with the
+// list.  Each instance i may run its own number of steps n_i; pass g of its
+// run is applied while g <= 2 n_i and skipped after.  The
 // launches of a kgs_batch_step_each call are captured once into a CUDA graph
 // and replayed while the instance set and step counts stay the same.  The
 // FP64 and FP32 launch sequences run on two streams forked from the caller's
@@ -117,47 +119,23 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, int64_t t, 
     in.uv[i] = b;
 }
 
-template <typename T, int D>
-__device__ __forceinline__ void batch_dispatch(const BatchInst<T>& in, int64_t t, int parity,
-                                               int mode)
-{
-    switch (mode) {
-    case RED_BASE: batch_update<T, D, RED_BASE>(in, t, parity); break;
-    case BLACK_FUSED: batch_update<T, D, BLACK_FUSED>(in, t, parity); break;
-    case RED_FUSED: batch_update<T, D, RED_FUSED>(in, t, parity); break;
-    default: batch_update<T, D, RED_ADJ>(in, t, parity); break;
-    }
-}
-
-// Pass g (colour: red for even g) of every instance of the list.
-template <typename T>
+// Pass g (colour: red for even g) of the instances of one list (one precision
+// and dimension) whose mode at pass g is MODE; chunk_inst gives each chunk's
+// instance, so a chunk's lookup is one load shared by the CTA.
+template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(kChunk) batch_pass_kernel(const BatchInst<T>* __restrict__ insts,
-                                                            int ninst, int64_t total_chunks,
-                                                            int64_t g)
+                                                            const int32_t* __restrict__ chunk_inst,
+                                                            int64_t total_chunks, int64_t g)
 {
-    __shared__ int s_inst;
+    const int red = red_parity(D);
+    const int parity = (g & 1) ? (red ^ 1) : red;
     for (int64_t ch = blockIdx.x; ch < total_chunks; ch += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = ninst - 1;  // last instance whose first chunk <= ch
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (insts[mid].first_chunk <= ch) lo = mid;
-                else hi = mid - 1;
-            }
-            s_inst = lo;
-        }
-        __syncthreads();
-        const BatchInst<T>& in = insts[s_inst];
-        __syncthreads();  // s_inst is rewritten in the next iteration
-        if (g > 2 * in.nsteps) continue;
-        const int mode = batch_mode(g, in.nsteps);
-        const int red = red_parity(in.dim);
-        const int parity = (g & 1) ? (red ^ 1) : red;
+        const BatchInst<T>& in = insts[__ldg(&chunk_inst[ch])];
+        const int64_t n = in.nsteps;
+        if (g > 2 * n || batch_mode(g, n) != MODE) continue;  // the same for the whole CTA
         const int64_t t = (ch - in.first_chunk) * kChunk + threadIdx.x;
         if (t >= in.half) continue;
-        if (in.dim == 1) batch_dispatch<T, 1>(in, t, parity, mode);
-        else if (in.dim == 2) batch_dispatch<T, 2>(in, t, parity, mode);
-        else batch_dispatch<T, 3>(in, t, parity, mode);
+        batch_update<T, D, MODE>(in, t, parity);
     }
 }
 
@@ -189,10 +167,15 @@ struct kgs_batch {
     size_t capacity = 0;
     std::map<size_t, size_t> free_ranges;  // offset -> length
     std::vector<HostInst> inst;
-    // device descriptors and work list per precision
-    BatchInst<double>* d64 = nullptr;
-    BatchInst<float>* d32 = nullptr;
-    int cap64 = 0, cap32 = 0;
+    // device work lists per precision (0: FP64, 1: FP32) and dimension: the
+    // instance descriptors and the instance of every chunk
+    struct DevList {
+        void* inst = nullptr;
+        int cap = 0;
+        int32_t* chunk_inst = nullptr;
+        int64_t chunk_cap = 0;
+    } lists[2][3];
+    int64_t graph_launches = 0;  // kernels per replay of the graph
     // stepping
     int ctas_per_sm = 8;
     int use_graph = 1;
@@ -290,81 +273,128 @@ Coef<double> coef64(const HostInst& h)
 
 Coef<float> coef32(const HostInst& h) { return host_coef32(coef64(h)); }
 
-template <typename T>
-void build_list(kgs_batch* b, const int64_t* nsteps, std::vector<BatchInst<T>>& list,
-                int64_t* total_chunks)
-{
-    list.clear();
+// Instances of one precision and dimension taking part in a call, in
+// instance order, with the instance of every chunk and the pass at which each
+// instance ends (2 n_i: its RED_ADJ pass).
+template <typename T> struct HostList {
+    std::vector<BatchInst<T>> inst;
+    std::vector<int32_t> chunk_inst;
+    std::vector<int64_t> ends;
     int64_t chunks = 0;
+};
+
+template <typename T>
+void build_lists(kgs_batch* b, const int64_t* nsteps, HostList<T> (&L)[3])
+{
     const int prec = sizeof(T) == 8 ? 64 : 32;
+    for (auto& l : L) l = HostList<T>();
     for (size_t i = 0; i < b->inst.size(); ++i) {
         const HostInst& h = b->inst[i];
         if (!h.live || h.precision != prec || nsteps[i] <= 0) continue;
+        HostList<T>& l = L[h.dim - 1];
         BatchInst<T> d;
         d.pq = reinterpret_cast<vec2_t<T>*>(b->arena + h.off);
         d.uv = d.pq + h.M;
         d.dim = h.dim;
         d.N = (int)h.N;
         d.half = h.M / 2;
-        d.first_chunk = chunks;
+        d.first_chunk = l.chunks;
         d.nsteps = nsteps[i];
         if constexpr (sizeof(T) == 8) d.coef = coef64(h);
         else d.coef = coef32(h);
-        list.push_back(d);
-        chunks += (d.half + kChunk - 1) / kChunk;
+        const int64_t c = (d.half + kChunk - 1) / kChunk;
+        l.chunk_inst.insert(l.chunk_inst.end(), (size_t)c, (int32_t)l.inst.size());
+        l.inst.push_back(d);
+        l.ends.push_back(2 * nsteps[i]);
+        l.chunks += c;
     }
-    *total_chunks = chunks;
 }
 
 template <typename T>
-int upload_list(kgs_batch* b, const std::vector<BatchInst<T>>& list, cudaStream_t s)
+int upload_list(kgs_batch* b, kgs_batch::DevList& dl, const HostList<T>& l, cudaStream_t s)
 {
-    BatchInst<T>*& dev = (sizeof(T) == 8) ? reinterpret_cast<BatchInst<T>*&>(b->d64)
-                                          : reinterpret_cast<BatchInst<T>*&>(b->d32);
-    int& cap = (sizeof(T) == 8) ? b->cap64 : b->cap32;
-    if ((int)list.size() > cap) {
-        cudaFree(dev);
-        dev = nullptr;
-        cap = 0;
-        const int want = std::max<int>((int)list.size(), 64);
-        cudaError_t e = cudaMalloc(&dev, want * sizeof(BatchInst<T>));
+    if (l.inst.empty()) return KGS_OK;
+    if ((int)l.inst.size() > dl.cap) {
+        cudaFree(dl.inst);
+        dl.inst = nullptr;
+        dl.cap = 0;
+        const int want = std::max<int>((int)l.inst.size(), 64);
+        cudaError_t e = cudaMalloc(&dl.inst, want * sizeof(BatchInst<T>));
         if (e != cudaSuccess) return bcuda(b, e, "batch descriptor allocation");
-        cap = want;
+        dl.cap = want;
     }
-    if (!list.empty()) {
-        cudaError_t e = cudaMemcpyAsync(dev, list.data(), list.size() * sizeof(BatchInst<T>),
-                                        cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return bcuda(b, e, "batch descriptor upload");
-        // the host vector must outlive the copy
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return bcuda(b, e, "batch descriptor upload");
+    if (l.chunks > dl.chunk_cap) {
+        cudaFree(dl.chunk_inst);
+        dl.chunk_inst = nullptr;
+        dl.chunk_cap = 0;
+        cudaError_t e = cudaMalloc(&dl.chunk_inst, (size_t)l.chunks * sizeof(int32_t));
+        if (e != cudaSuccess) return bcuda(b, e, "batch work list allocation");
+        dl.chunk_cap = l.chunks;
     }
+    cudaError_t e = cudaMemcpyAsync(dl.inst, l.inst.data(), l.inst.size() * sizeof(BatchInst<T>),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dl.chunk_inst, l.chunk_inst.data(), (size_t)l.chunks * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
+    // the host vectors must outlive the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(b, e, "batch work list upload");
     return KGS_OK;
 }
 
-template <typename T>
-int launch_batch_pass(kgs_batch* b, int ninst, int64_t chunks, int64_t g, cudaStream_t s)
+template <typename T, int D, int MODE>
+int launch_one(kgs_batch* b, const kgs_batch::DevList& dl, int64_t chunks, int64_t g, cudaStream_t s)
 {
-    if (ninst == 0 || chunks == 0) return KGS_OK;
-    const BatchInst<T>* dev = (sizeof(T) == 8) ? reinterpret_cast<const BatchInst<T>*>(b->d64)
-                                               : reinterpret_cast<const BatchInst<T>*>(b->d32);
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     const int64_t grid = std::min<int64_t>(chunks, (int64_t)sms * b->ctas_per_sm);
-    batch_pass_kernel<T><<<(unsigned)grid, kChunk, 0, s>>>(dev, ninst, chunks, g);
+    batch_pass_kernel<T, D, MODE><<<(unsigned)grid, kChunk, 0, s>>>(
+        reinterpret_cast<const BatchInst<T>*>(dl.inst), dl.chunk_inst, chunks, g);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return bcuda(b, e, "batch pass launch");
     b->launches += 1;
     return KGS_OK;
 }
 
+// Pass g of one list: one launch per pass mode that occurs among its instances.
+template <typename T, int D>
+int launch_list_pass(kgs_batch* b, const kgs_batch::DevList& dl, const HostList<T>& l, int64_t g,
+                     cudaStream_t s)
+{
+    if (l.chunks == 0) return KGS_OK;
+    bool later = false, ending = false;
+    for (int64_t e : l.ends) {
+        later = later || e > g;
+        ending = ending || e == g;
+    }
+    if (g == 0) return launch_one<T, D, RED_BASE>(b, dl, l.chunks, g, s);
+    if (g & 1) return later ? launch_one<T, D, BLACK_FUSED>(b, dl, l.chunks, g, s) : KGS_OK;
+    int r = later ? launch_one<T, D, RED_FUSED>(b, dl, l.chunks, g, s) : KGS_OK;
+    if (!r && ending) r = launch_one<T, D, RED_ADJ>(b, dl, l.chunks, g, s);
+    return r;
+}
+
+template <typename T>
+int launch_pass_all(kgs_batch* b, const HostList<T> (&L)[3], int64_t g, cudaStream_t s)
+{
+    kgs_batch::DevList* dl = b->lists[sizeof(T) == 8 ? 0 : 1];
+    int r = launch_list_pass<T, 1>(b, dl[0], L[0], g, s);
+    if (!r) r = launch_list_pass<T, 2>(b, dl[1], L[1], g, s);
+    if (!r) r = launch_list_pass<T, 3>(b, dl[2], L[2], g, s);
+    return r;
+}
+
 int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
 {
-    std::vector<BatchInst<double>> l64;
-    std::vector<BatchInst<float>> l32;
+    HostList<double> l64[3];
+    HostList<float> l32[3];
+    build_lists(b, nsteps, l64);
+    build_lists(b, nsteps, l32);
     int64_t c64 = 0, c32 = 0, nmax = 0;
-    build_list(b, nsteps, l64, &c64);
-    build_list(b, nsteps, l32, &c32);
+    for (int d = 0; d < 3; ++d) {
+        c64 += l64[d].chunks;
+        c32 += l32[d].chunks;
+    }
     for (size_t i = 0; i < b->inst.size(); ++i)
         if (b->inst[i].live) nmax = std::max(nmax, nsteps[i]);
     if (nmax == 0) return KGS_OK;
@@ -375,11 +405,14 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     if (b->use_graph && b->graph && key == b->graph_key) {
         cudaError_t e = cudaGraphLaunch(b->graph, s);
         if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
-        b->launches += passes * ((c64 ? 1 : 0) + (c32 ? 1 : 0));
+        b->launches += b->graph_launches;
         return KGS_OK;
     }
-    int st = upload_list(b, l64, s);
-    if (!st) st = upload_list(b, l32, s);
+    int st = KGS_OK;
+    for (int d = 0; d < 3 && !st; ++d) {
+        st = upload_list(b, b->lists[0][d], l64[d], s);
+        if (!st) st = upload_list(b, b->lists[1][d], l32[d], s);
+    }
     if (st) return st;
     // FP64 passes (bound by the FP64 pipe) on the caller's stream, FP32 passes
     // (bound by DRAM) on a second stream forked from it, so the two precisions
@@ -401,8 +434,8 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
         }
         int r = KGS_OK;
         for (int64_t g = 0; g < passes && !r; ++g) {
-            r = launch_batch_pass<double>(b, (int)l64.size(), c64, g, main);
-            if (!r) r = launch_batch_pass<float>(b, (int)l32.size(), c32, g, s32);
+            r = launch_pass_all<double>(b, l64, g, main);
+            if (!r) r = launch_pass_all<float>(b, l32, g, s32);
         }
         if (r) return r;
         if (both) {
@@ -424,6 +457,7 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     st = issue(b->capture_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->capture_stream, &graph);
+    b->graph_launches = b->launches - before;
     b->launches = before;
     if (st) {
         if (graph) cudaGraphDestroy(graph);
@@ -439,7 +473,7 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     b->graph_key = key;
     e = cudaGraphLaunch(b->graph, s);
     if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
-    b->launches += passes * ((c64 ? 1 : 0) + (c32 ? 1 : 0));
+    b->launches += b->graph_launches;
     return KGS_OK;
 }
 
@@ -756,8 +790,11 @@ void kgs_batch_destroy(kgs_batch_handle b)
         if (b->fork) cudaEventDestroy(b->fork);
         if (b->join) cudaEventDestroy(b->join);
         cudaFree(b->arena);
-        cudaFree(b->d64);
-        cudaFree(b->d32);
+        for (auto& row : b->lists)
+            for (auto& dl : row) {
+                cudaFree(dl.inst);
+                cudaFree(dl.chunk_inst);
+            }
         cudaFree(b->scratch);
         cudaFree(b->out_dev);
         if (b->out_host) cudaFreeHost(b->out_host);
