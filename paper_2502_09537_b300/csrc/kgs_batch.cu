@@ -58,11 +58,11 @@ __device__ __forceinline__ int batch_mode(int64_t g, int64_t n)
 // Linear index and neighbours of the t-th point of a colour (0-based index sum
 // parity `parity`) -- the same point order and neighbour order as the solo
 // pass kernel; rows along the last axis, N/2 points of each colour per row.
-template <int D>
-__device__ __forceinline__ int64_t batch_point(int64_t t, int N, int parity, int64_t nb[2 * D])
+template <int D, typename I>
+__device__ __forceinline__ I batch_point(I t, int N, int parity, I nb[2 * D])
 {
-    const int hN = N >> 1;
-    const int64_t row = t / hN;
+    const I hN = (I)(N >> 1);
+    const I row = t / hN;
     const int kk = (int)(t - row * hN);
     int i0 = 0, i1 = 0, rp = 0;
     if (D == 2) {
@@ -70,14 +70,14 @@ __device__ __forceinline__ int64_t batch_point(int64_t t, int N, int parity, int
         rp = i0 & 1;
     } else if (D == 3) {
         i0 = (int)(row / N);
-        i1 = (int)(row - (int64_t)i0 * N);
+        i1 = (int)(row - (I)i0 * N);
         rp = (i0 + i1) & 1;
     }
     const int k = 2 * kk + ((parity - rp) & 1);
-    const int64_t n = N;
-    const int64_t i = row * n + k;
-    const int64_t km = (k == 0) ? i + (n - 1) : i - 1;
-    const int64_t kp = (k == N - 1) ? i - (n - 1) : i + 1;
+    const I n = N;
+    const I i = row * n + k;
+    const I km = (k == 0) ? i + (n - 1) : i - 1;
+    const I kp = (k == N - 1) ? i - (n - 1) : i + 1;
     if (D == 1) {
         nb[0] = km;
         nb[1] = kp;
@@ -87,7 +87,7 @@ __device__ __forceinline__ int64_t batch_point(int64_t t, int N, int parity, int
         nb[2] = km;
         nb[3] = kp;
     } else {
-        const int64_t n2 = n * n;
+        const I n2 = n * n;
         nb[0] = (i0 == 0) ? i + (n - 1) * n2 : i - n2;
         nb[1] = (i0 == N - 1) ? i - (n - 1) * n2 : i + n2;
         nb[2] = (i1 == 0) ? i + (n - 1) * n : i - n;
@@ -98,11 +98,11 @@ __device__ __forceinline__ int64_t batch_point(int64_t t, int N, int parity, int
     return i;
 }
 
-template <typename T, int D, int MODE>
-__device__ __forceinline__ void batch_update(const BatchInst<T>& in, int64_t t, int parity)
+template <typename T, int D, int MODE, typename I>
+__device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int parity)
 {
-    int64_t nb[2 * D];
-    const int64_t i = batch_point<D>(t, in.N, parity, nb);
+    I nb[2 * D];
+    const I i = batch_point<D, I>(t, in.N, parity, nb);
     const T* u = reinterpret_cast<const T*>(in.uv);
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
@@ -122,8 +122,9 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, int64_t t, 
 // Pass g (colour: red for even g) of the instances of one list (one precision
 // and dimension) whose mode at pass g is MODE; chunk_inst gives each chunk's
 // instance, so a chunk's lookup is one load shared by the CTA.
-template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(kChunk) batch_pass_kernel(const BatchInst<T>* __restrict__ insts,
+// I: index type, int32_t when every instance of the list has fewer than 2^31 points.
+template <typename T, int D, int MODE, typename I>
+__global__ void __launch_bounds__(kChunk, 4) batch_pass_kernel(const BatchInst<T>* __restrict__ insts,
                                                             const int32_t* __restrict__ chunk_inst,
                                                             int64_t total_chunks, int64_t g)
 {
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kChunk) batch_pass_kernel(const BatchInst<T>* 
         if (g > 2 * n || batch_mode(g, n) != MODE) continue;  // the same for the whole CTA
         const int64_t t = (ch - in.first_chunk) * kChunk + threadIdx.x;
         if (t >= in.half) continue;
-        batch_update<T, D, MODE>(in, t, parity);
+        batch_update<T, D, MODE, I>(in, (I)t, parity);
     }
 }
 
@@ -281,6 +282,7 @@ template <typename T> struct HostList {
     std::vector<int32_t> chunk_inst;
     std::vector<int64_t> ends;
     int64_t chunks = 0;
+    bool wide = false;  // an instance has 2^31 points or more: 64-bit indices
 };
 
 template <typename T>
@@ -307,6 +309,7 @@ void build_lists(kgs_batch* b, const int64_t* nsteps, HostList<T> (&L)[3])
         l.inst.push_back(d);
         l.ends.push_back(2 * nsteps[i]);
         l.chunks += c;
+        l.wide = l.wide || h.M >= ((int64_t)1 << 31);
     }
 }
 
@@ -343,13 +346,17 @@ int upload_list(kgs_batch* b, kgs_batch::DevList& dl, const HostList<T>& l, cuda
 }
 
 template <typename T, int D, int MODE>
-int launch_one(kgs_batch* b, const kgs_batch::DevList& dl, int64_t chunks, int64_t g, cudaStream_t s)
+int launch_one(kgs_batch* b, const kgs_batch::DevList& dl, int64_t chunks, bool wide, int64_t g,
+               cudaStream_t s)
 {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     const int64_t grid = std::min<int64_t>(chunks, (int64_t)sms * b->ctas_per_sm);
-    batch_pass_kernel<T, D, MODE><<<(unsigned)grid, kChunk, 0, s>>>(
-        reinterpret_cast<const BatchInst<T>*>(dl.inst), dl.chunk_inst, chunks, g);
+    const BatchInst<T>* insts = reinterpret_cast<const BatchInst<T>*>(dl.inst);
+    if (wide)
+        batch_pass_kernel<T, D, MODE, int64_t><<<(unsigned)grid, kChunk, 0, s>>>(insts, dl.chunk_inst, chunks, g);
+    else
+        batch_pass_kernel<T, D, MODE, int32_t><<<(unsigned)grid, kChunk, 0, s>>>(insts, dl.chunk_inst, chunks, g);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return bcuda(b, e, "batch pass launch");
     b->launches += 1;
@@ -367,10 +374,10 @@ int launch_list_pass(kgs_batch* b, const kgs_batch::DevList& dl, const HostList<
         later = later || e > g;
         ending = ending || e == g;
     }
-    if (g == 0) return launch_one<T, D, RED_BASE>(b, dl, l.chunks, g, s);
-    if (g & 1) return later ? launch_one<T, D, BLACK_FUSED>(b, dl, l.chunks, g, s) : KGS_OK;
-    int r = later ? launch_one<T, D, RED_FUSED>(b, dl, l.chunks, g, s) : KGS_OK;
-    if (!r && ending) r = launch_one<T, D, RED_ADJ>(b, dl, l.chunks, g, s);
+    if (g == 0) return launch_one<T, D, RED_BASE>(b, dl, l.chunks, l.wide, g, s);
+    if (g & 1) return later ? launch_one<T, D, BLACK_FUSED>(b, dl, l.chunks, l.wide, g, s) : KGS_OK;
+    int r = later ? launch_one<T, D, RED_FUSED>(b, dl, l.chunks, l.wide, g, s) : KGS_OK;
+    if (!r && ending) r = launch_one<T, D, RED_ADJ>(b, dl, l.chunks, l.wide, g, s);
     return r;
 }
 
