@@ -48,7 +48,7 @@ int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
  * integer accumulator (then it is the correctly rounded sum of the row) and
  * bit 1 = beta S was (then it is beta times the exact sum, rounded once);
  * where a bit is 0 the left-to-right float64 sum (times beta, rounded) was
- * taken: an infinite, NaN or subnormal value, a nonzero value more than 71
+ * taken: an infinite or NaN value, a nonzero value more than 31
  * binades below the row's largest, a zero or subnormal beta, or a result
  * outside the normal range.  A row whose entry points disagreed with these
  * halves reads -1.  Host buffers are the caller's; the call copies through

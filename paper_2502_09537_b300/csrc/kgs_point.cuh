@@ -96,13 +96,13 @@ __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 // Each value is split into sign, exponent and significand (subnormals exactly,
 // as exponent 1 without the hidden bit), shifted to the largest exponent in a
 // signed 96-bit fixed-point accumulator held in three 32-bit words (the
-// largest significand's leading bit at bit 91, so up to 6 terms cannot
-// overflow and any term within 39 binades of the largest is added exactly)
+// largest significand's leading bit at bit 83, so up to 6 terms cannot
+// overflow and any term within 31 binades of the largest is added exactly)
 // and added with the PTX carry chain (add.cc/addc; a negative term enters as
-// its one's complement with the carry-in set by its sign).  The exact sum is
+// its one's complement, the +1s added once at the end).  The exact sum is
 // then rounded once, or multiplied exactly by beta's significand (64 x 53
 // bits) and rounded once.  Where that does not apply -- an input is infinite
-// or NaN, a nonzero term lies more than 39 binades below the largest, beta is
+// or NaN, a nonzero term lies more than 31 binades below the largest, beta is
 // zero or subnormal, or the result is not a normal number -- the
 // left-to-right FP64 sum (times beta, rounded) is taken instead, in a
 // function call so that the compiler cannot execute it speculatively for
@@ -146,17 +146,15 @@ struct ExactSum {
     bool zero, negzero, ok;
 };
 
-// (a2:a1:a0) += (x2:x1:x0) + (s & 1), s = 0 or all ones: one carry chain.
-__device__ __forceinline__ void add96_cin(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t x0,
-                                          uint32_t x1, uint32_t x2, uint32_t s)
+// (a2:a1:a0) += (x2:x1:x0): one carry chain.
+__device__ __forceinline__ void add96(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t x0, uint32_t x1,
+                                      uint32_t x2)
 {
-    asm("{\n\t.reg .u32 t;\n\t"
-        "add.cc.u32 t, %3, %3;\n\t"  // carry = top bit of s
-        "addc.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, %5;\n\t"
-        "addc.u32 %2, %2, %6;\n\t}"
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, %5;"
         : "+r"(a0), "+r"(a1), "+r"(a2)
-        : "r"(s), "r"(x0), "r"(x1), "r"(x2));
+        : "r"(x0), "r"(x1), "r"(x2));
 }
 
 template <int K>
@@ -166,7 +164,7 @@ __device__ __forceinline__ ExactSum exact_sum(const double (&v)[K])
     uint32_t hi[K], lo[K];
     int e[K];
     int emax = 1, emin = 0x7FF;  // largest exponent; smallest of a nonzero term
-    bool allnz = true;
+    uint32_t hand = 0xFFFFFFFFu, lor = 0u;  // AND of the high words; OR of the magnitude bits
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         hi[i] = (uint32_t)__double2hiint(v[i]);
@@ -174,34 +172,37 @@ __device__ __forceinline__ ExactSum exact_sum(const double (&v)[K])
         e[i] = (int)(hi[i] >> 20) & 0x7FF;
         const int ei = e[i] > 1 ? e[i] : 1;  // subnormal: exponent 1, no hidden bit
         emax = ei > emax ? ei : emax;
-        const bool nz = ((hi[i] << 1) | lo[i]) != 0u;
-        emin = (nz && ei < emin) ? ei : emin;
-        allnz = allnz && hi[i] == 0x80000000u && lo[i] == 0u;
+        const uint32_t mag = (hi[i] << 1) | lo[i];  // 0 only for +-0
+        const int key = mag ? ei : 0x7FF;
+        emin = key < emin ? key : emin;
+        hand &= hi[i];
+        lor |= mag;
     }
     ExactSum r;
-    r.ok = emax != 0x7FF && emax - emin <= 39;  // holds for all-zero rows (emin = 0x7FF)
-    // signed 96-bit accumulator (a2:a1:a0), unit 2^(emax - 1114)
-    uint32_t a0 = 0, a1 = 0, a2 = 0;
+    r.ok = emax != 0x7FF && emax - emin <= 31;  // holds for all-zero rows (emin = 0x7FF)
+    // signed 96-bit accumulator (a2:a1:a0), unit 2^(emax - 1106): a term's
+    // significand shifted left by 31 - (emax - e) <= 31 stays in three words
+    // and six terms stay below 2^87.  A negative term enters as its one's
+    // complement; the +1s of the two's complements are added once at the end.
+    uint32_t a0 = 0, a1 = 0, a2 = 0, nneg = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const uint32_t mh = (hi[i] & 0xFFFFFu) | (e[i] ? 0x100000u : 0u);
         const int ei = e[i] > 1 ? e[i] : 1;
-        int sh = 39 - emax + ei;
-        sh = sh > 0 ? sh : 0;  // terms below the window are zeros, or the row is not ok
-        const uint32_t b = (uint32_t)sh & 31u;
-        const uint32_t w0 = lo[i] << b;
-        const uint32_t w1 = __funnelshift_l(lo[i], mh, b);
-        const uint32_t w2 = __funnelshift_l(mh, 0u, b);
-        const bool q = sh >= 32;  // then b <= 7 and w2 = 0
+        // a zero term shifts anything by anything; a nonzero one below the
+        // window has made the row not ok
+        const uint32_t b = (uint32_t)(31 - emax + ei) & 31u;
         const uint32_t s = (uint32_t)((int32_t)hi[i] >> 31);
-        add96_cin(a0, a1, a2, (q ? 0u : w0) ^ s, (q ? w0 : w1) ^ s, (q ? w1 : w2) ^ s, s);
+        add96(a0, a1, a2, (lo[i] << b) ^ s, __funnelshift_l(lo[i], mh, b) ^ s, __funnelshift_l(mh, 0u, b) ^ s);
+        nneg -= s;
     }
+    add96(a0, a1, a2, nneg, 0u, 0u);
     const uint32_t sm = (uint32_t)((int32_t)a2 >> 31);
     r.sgn = sm & 1u;
-    uint32_t m0 = 0, m1 = 0, m2 = 0;  // magnitude
-    add96_cin(m0, m1, m2, a0 ^ sm, a1 ^ sm, a2 ^ sm, sm);
+    uint32_t m0 = a0 ^ sm, m1 = a1 ^ sm, m2 = a2 ^ sm;  // magnitude: one's complement + 1
+    add96(m0, m1, m2, sm & 1u, 0u, 0u);
     r.zero = (m0 | m1 | m2) == 0u;
-    r.negzero = allnz;
+    r.negzero = lor == 0u && (hand >> 31) != 0u;
     // normalise: the leading word, then the bits below its leading one
     const bool w2nz = m2 != 0u, w1nz = m1 != 0u;
     const uint32_t p2 = w2nz ? m2 : (w1nz ? m1 : m0);
@@ -214,7 +215,7 @@ __device__ __forceinline__ ExactSum exact_sum(const double (&v)[K])
     const uint32_t n0 = p0 << (cb & 31);
     r.h = ((uint64_t)n2 << 32) | n1;
     r.l = (uint64_t)n0 << 32;
-    r.er = emax + 4 - c;
+    r.er = emax + 12 - c;
     return r;
 }
 

@@ -73,13 +73,13 @@ def _biased_exponent(x):
 
 def _fast_path_expected(row):
     """Whether the exact accumulator must take the row: finite values whose
-    nonzero members lie within 39 binades of the largest (a subnormal counts
+    nonzero members lie within 31 binades of the largest (a subnormal counts
     as exponent 1), and an exact sum that is zero or has a normal exponent."""
     if not all(math.isfinite(v) for v in row):
         return False
     es = [max(_biased_exponent(v), 1) for v in row]
     nz = [e for e, v in zip(es, row) if v != 0.0]
-    if nz and max(es) - min(nz) > 39:
+    if nz and max(es) - min(nz) > 31:
         return False
     f = sum(Fraction(v) for v in row)
     if f == 0:
