@@ -6,9 +6,8 @@
  * (and the FP32 rate) the way a roofline denominator is usually taken: many
  * independent fused multiply-add chains per thread, enough CTAs to fill every
  * SM, timed with CUDA events on the given stream.  The other entry points
- * expose the float64 reciprocal, neighbour sums and Psi weight of the colour
- * passes so that tests can check them against IEEE division and exact
- * arithmetic.
+ * expose the float64 neighbour sums and Psi weight of the colour passes so
+ * that tests can check them against exact arithmetic.
  */
 #ifndef KGS_PROBE_H
 #define KGS_PROBE_H
@@ -28,16 +27,6 @@ extern "C" {
  * precision not 32/64, NULL outputs) or -4 if a CUDA call failed. */
 int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* stream,
                        double* elapsed_ms, double* fma_per_s);
-
-/* Accuracy of the float64 reciprocal the colour passes use for 1/(1 + r^2):
- * evaluates it on n arguments d = 1 + r^2, r spread over [-rmax, rmax] by a
- * fixed hash of the sample index, against CUDA's IEEE division 1.0/d, on the
- * current device and stream (synchronised).  Writes the largest difference in
- * units in the last place and the number of samples that differ at all.
- * Returns 0, -1 for a bad argument (n < 1, rmax not finite or <= 0, NULL
- * outputs) or -4 if a CUDA call failed. */
-int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
-                      int64_t* n_differ);
 
 /* The float64 neighbour sums of the colour passes on n rows of k values
  * (k = 2, 4 or 6, the 2d neighbours of a point in 1, 2 or 3 dimensions):

@@ -60,23 +60,7 @@ __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
-// Reciprocal of a >= 1 in float64: the hardware estimate (rcp.approx.ftz.f64,
-// about 20 correct bits from the high word) refined by one step of the
-// cubically convergent Newton-Raphson iteration for 1/a,
-//   e = 1 - a y,   y <- y + y (e + e^2)
-// (J.-M. Muller et al., Handbook of Floating-Point Arithmetic, ch. on Newton-
-// Raphson division), whose error after the step is about e^3 ~ 2^-60 before
-// the final rounding: within one ulp of the IEEE quotient (kgs_probe.h
-// measures it against CUDA's division).  Three FP64 FMAs instead of the
-// longer correctly rounded sequence; here the reciprocal only scales an
-// increment, so one ulp in it is far below one ulp of the state.
-__device__ __forceinline__ double rcp_(double a)
-{
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    const double e = __fma_rn(-a, y, 1.0);
-    return __fma_rn(y, __fma_rn(e, e, e), y);
-}
+// Reciprocal in float32 (the float64 passes form 1/(1 + r^2) by psi_weight).
 __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 
 // ---------------------------------------------------- neighbour sums --

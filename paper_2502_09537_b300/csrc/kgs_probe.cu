@@ -1,7 +1,7 @@
 // kgs_probe.cu -- probes declared in include/kgs_probe.h: the FMA issue rate
 // (the FP64 pipe rate that bounds the float64 colour passes, for the roofline
-// denominator) and the colour passes' float64 reciprocal, neighbour sums and
-// Psi weight exposed for accuracy tests.
+// denominator) and the colour passes' float64 neighbour sums and Psi weight
+// exposed for accuracy tests.
 #include "../../include/kgs_probe.h"
 
 #include <cuda_runtime.h>
@@ -46,34 +46,6 @@ int run(int64_t iters, int bps, cudaStream_t s, double* ms, double* rate)
     *ms = t;
     *rate = (double)blocks * 256.0 * 8.0 * (double)iters / (t * 1e-3);
     return 0;
-}
-
-__device__ __forceinline__ uint64_t mix64(uint64_t x)
-{
-    x += 0x9e3779b97f4a7c15ull;
-    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
-    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
-    return x ^ (x >> 31);
-}
-
-__global__ void rcp_ulp_kernel(int64_t n, double rmax, unsigned long long* max_ulp,
-                               unsigned long long* n_differ)
-{
-    unsigned long long worst = 0, differ = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double u = (double)(mix64((uint64_t)i) >> 11) * 0x1.0p-53;  // [0, 1)
-        const double r = (2.0 * u - 1.0) * rmax;
-        const double d = __fma_rn(r, r, 1.0);
-        const double want = 1.0 / d;
-        const double got = kgs::rcp_(d);
-        const long long a = __double_as_longlong(want), b = __double_as_longlong(got);
-        const unsigned long long diff = (unsigned long long)(a > b ? a - b : b - a);
-        worst = diff > worst ? diff : worst;
-        differ += diff != 0;
-    }
-    atomicMax(max_ulp, worst);
-    atomicAdd(n_differ, differ);
 }
 
 template <int K>
@@ -162,28 +134,6 @@ extern "C" int kgs_probe_nsum(int k, int64_t n, const double* x_host, double bet
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dev);
     return e == cudaSuccess ? 0 : -4;
-}
-
-extern "C" int kgs_probe_rcp_ulp(int64_t n, double rmax, void* stream, int64_t* max_ulp,
-                                 int64_t* n_differ)
-{
-    if (n < 1 || !(rmax > 0) || rmax > 1e150 || !max_ulp || !n_differ) return -1;
-    unsigned long long* dev = nullptr;
-    if (cudaMalloc(&dev, 2 * sizeof(unsigned long long)) != cudaSuccess) return -4;
-    cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long host[2] = {0, 0};
-    cudaError_t e = cudaMemsetAsync(dev, 0, 2 * sizeof(unsigned long long), s);
-    if (e == cudaSuccess) {
-        rcp_ulp_kernel<<<148 * 4, 256, 0, s>>>(n, rmax, dev, dev + 1);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host, dev, sizeof host, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(dev);
-    if (e != cudaSuccess) return -4;
-    *max_ulp = (int64_t)host[0];
-    *n_differ = (int64_t)host[1];
-    return 0;
 }
 
 extern "C" int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_sm, void* stream,

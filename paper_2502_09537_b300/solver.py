@@ -74,8 +74,6 @@ SIGNATURES = {
     "kgs_batch_destroy": (None, [_vp]),
     # include/kgs_probe.h
     "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
-    "kgs_probe_rcp_ulp": (ctypes.c_int, [_c_int64, _c_dbl, _vp, ctypes.POINTER(_c_int64),
-                                         ctypes.POINTER(_c_int64)]),
     "kgs_probe_nsum": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _c_dbl, _vp, _vp, _vp, _vp]),
     "kgs_probe_psi_weight": (ctypes.c_int, [_c_int64, _vp, _vp, _vp]),
 }
@@ -266,17 +264,6 @@ def probe_fma_rate(precision: int = 64, iters: int = 4096, blocks_per_sm: int = 
     if st != 0:
         raise KGSError(st, "FMA probe failed")
     return rate.value, ms.value
-
-
-def probe_rcp_ulp(n: int = 1 << 24, rmax: float = 100.0, stream=None):
-    """(max ulp difference, number of differing samples) of the float64
-    reciprocal the colour passes use, against CUDA's IEEE division."""
-    lib = load_library()
-    mx, nd = ctypes.c_int64(), ctypes.c_int64()
-    st = lib.kgs_probe_rcp_ulp(n, rmax, _stream_ptr(stream), ctypes.byref(mx), ctypes.byref(nd))
-    if st != 0:
-        raise KGSError(st, "reciprocal probe failed")
-    return mx.value, nd.value
 
 
 def probe_nsum(x, beta: float = 1.0, stream=None):
