@@ -68,9 +68,7 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 # DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
 # ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
 # the kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("2d", "fp64"): 134.38e6 + 74.17e6,   # pass_kernel_fp64_kgs2d_N2048.md
-               ("3d", "fp64"): 8 * (541.1e6 + 478.5e6),  # pass_kernel_fp64_kgs3d_N256.md, x8 points
-               ("3d", "fp32"): 2.156e9 + 2.091e9}     # pass_kernel_fp32_kgs3d_N512.md
+NCU_TRAFFIC = {("3d", "fp32"): 2.1518e9 + 1.0394e9}   # pass_kernel_fp32_kgs3d_N512.md
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), 148 SMs, 2032 MHz maximum SM

@@ -1,7 +1,8 @@
 // kgs_api.cu -- the C ABI of libkgs (declared and documented in include/kgs.h).
 //
 // A handle owns its device state ((P,Q) and (U,V) as vec2 arrays in the state
-// precision), a float64 staging buffer for layout conversion, and reduction
+// precision, in the colour-split layout of kgs_internal.h: each colour's points
+// contiguous), a float64 staging buffer for layout conversion, and reduction
 // scratch.  kgs_step issues the fused colour passes of a checkerboard DP-AVF2
 // run (RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ; see
 // kgs_point.cuh): small grids as one shared-memory resident launch, larger
@@ -133,6 +134,7 @@ Grid grid_of(const kgs_solver* h)
     Grid g{h->dim, h->N, h->M};
     g.threads = h->opt_threads;
     g.persistent = kernel_choice(h) == 4;
+    g.split = true;  // a handle's state is in the colour-split layout
     return g;
 }
 
@@ -379,6 +381,17 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
         TileParams tp = h->tile_set ? h->tile : default_tile(h->dim, h->precision);
         const int64_t passes = 2 * nsteps + 1;
         const int per = tp.H;
+        // the tile kernel works on natural order: convert into the other buffer
+        // pair, run, convert back (the state ends in buffer pair cur)
+        {
+            const int o = h->cur ^ 1;
+            if (launch_split_convert<T>(grid_of(h), false, (const vec2_t<T>*)h->pqb[h->cur],
+                                        (const vec2_t<T>*)h->uvb[h->cur], (vec2_t<T>*)h->pqb[o],
+                                        (vec2_t<T>*)h->uvb[o], s) < 0)
+                return cuda_fail(h, cudaGetLastError(), "layout conversion");
+            h->launches += 1;
+            h->cur = o;
+        }
         for (int64_t g0 = 0; g0 < passes; g0 += per) {
             tp.g0 = g0;
             tp.nsteps = nsteps;
@@ -394,6 +407,15 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
                 return cuda_fail(h, e, "tile kernel launch");
             }
             h->launches += n;
+            h->cur = o;
+        }
+        {
+            const int o = h->cur ^ 1;
+            if (launch_split_convert<T>(grid_of(h), true, (const vec2_t<T>*)h->pqb[h->cur],
+                                        (const vec2_t<T>*)h->uvb[h->cur], (vec2_t<T>*)h->pqb[o],
+                                        (vec2_t<T>*)h->uvb[o], s) < 0)
+                return cuda_fail(h, cudaGetLastError(), "layout conversion");
+            h->launches += 1;
             h->cur = o;
         }
         return KGS_OK;
@@ -541,8 +563,8 @@ int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* 
         }
         void* dst = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
-                    ? launch_pack<double>(h->M, (double2*)dst, f & 1, d, s)
-                    : launch_pack<float>(h->M, (float2*)dst, f & 1, d, s);
+                    ? launch_pack<double>(h->M, (double2*)dst, f & 1, d, s, h->dim, h->N)
+                    : launch_pack<float>(h->M, (float2*)dst, f & 1, d, s, h->dim, h->N);
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "pack launch");
         h->launches += n;
     }
@@ -570,8 +592,8 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int 
         double* d = (where == KGS_HOST) ? h->stage : dst[f];
         const void* src = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
-                    ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s)
-                    : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s);
+                    ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s, h->dim, h->N)
+                    : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s, h->dim, h->N);
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "unpack launch");
         h->launches += n;
         if (where == KGS_HOST) {

@@ -20,7 +20,25 @@ struct Grid {
     // axis-0 planes a colour pass covers: [plane0, plane0 + planes); planes = 0
     // means all N (one-launch-per-pass kernels only; 2D and 3D)
     int64_t plane0 = 0, planes = 0;
+    bool split = false;  // state in the colour-split layout (below)
 };
+
+// Colour-split state layout (a handle's vec2 arrays (P,Q) and (U,V)): the
+// points of even coordinate sum first, then those of odd coordinate sum, each
+// colour in natural (C) order; with N even, point i sits at
+// (parity(i) ? M/2 : 0) + (i >> 1).  A colour pass then reads and writes its
+// own colour's contiguous half and gathers the other half's neighbours with
+// consecutive threads on consecutive elements.
+__host__ __device__ __forceinline__ int point_parity(int64_t i, int dim, int64_t N)
+{
+    if (dim == 1) return (int)(i & 1);
+    if (dim == 2) return (int)((i + i / N) & 1);
+    return (int)((i + i / N + i / (N * N)) & 1);
+}
+__host__ __device__ __forceinline__ int64_t split_pos(int64_t i, int dim, int64_t N, int64_t half)
+{
+    return (point_parity(i, dim, N) ? half : 0) + (i >> 1);
+}
 
 // Largest point count the shared-memory resident kernel takes for state type T
 // (whole (P,Q) and (U,V) arrays in one CTA's shared memory).
@@ -66,11 +84,19 @@ template <typename T>
 int launch_level(int dim, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t* list, int64_t count,
                  int64_t N, const Coef<T>& c, cudaStream_t s);
 
-// Layout conversion (kgs_layout.cu): one float64 field <-> one component of a vec2 array.
+// Layout conversion (kgs_layout.cu): one float64 field <-> one component of a
+// vec2 array, natural order on the float64 side; dim > 0 puts the vec2 side in
+// the colour-split layout of an N^dim grid.  launch_split_convert: whole (P,Q)
+// and (U,V) arrays between the two layouts (to_split: natural -> split).
 template <typename T>
-int launch_pack(int64_t M, vec2_t<T>* dst, int comp, const double* src, cudaStream_t stream);
+int launch_pack(int64_t M, vec2_t<T>* dst, int comp, const double* src, cudaStream_t stream,
+                int dim = 0, int64_t N = 0);
 template <typename T>
-int launch_unpack(int64_t M, double* dst, const vec2_t<T>* src, int comp, cudaStream_t stream);
+int launch_unpack(int64_t M, double* dst, const vec2_t<T>* src, int comp, cudaStream_t stream,
+                  int dim = 0, int64_t N = 0);
+template <typename T>
+int launch_split_convert(const Grid& g, bool to_split, const vec2_t<T>* pq_in, const vec2_t<T>* uv_in,
+                         vec2_t<T>* pq_out, vec2_t<T>* uv_out, cudaStream_t stream);
 
 // Invariants (kgs_reduce.cu): E_h, its absolute-term scale, and the mass.
 struct InvParams {

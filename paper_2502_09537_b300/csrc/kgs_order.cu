@@ -54,21 +54,26 @@ __global__ void __launch_bounds__(256) level_kernel(vec2_t<T>* pq, vec2_t<T>* uv
     const int64_t i = list[k];
     int64_t nb[2 * D];
     neighbours_of<D>(i, N, nb);
+    // the handle's colour-split layout: the neighbours are in the other half
+    const int64_t half = (D == 1 ? N : (D == 2 ? N * N : N * N * N)) >> 1;
+    const int par = point_parity(i, D, N);
+    const int64_t own = (par ? half : 0) + (i >> 1), oth = par ? 0 : half;
     const T* u = reinterpret_cast<const T*>(uv);
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
-        const vec2_t<T> b = pq[nb[m]];
+        const int64_t j = oth + (nb[m] >> 1);
+        const vec2_t<T> b = pq[j];
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = u[2 * nb[m]];
+        w[m] = u[2 * j];
     }
-    vec2_t<T> a = pq[i];
-    vec2_t<T> b = uv[i];
+    vec2_t<T> a = pq[own];
+    vec2_t<T> b = uv[own];
     update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x,
                              a.y, b.x, b.y);
-    pq[i] = a;
-    uv[i] = b;
+    pq[own] = a;
+    uv[own] = b;
 }
 
 template <int D>

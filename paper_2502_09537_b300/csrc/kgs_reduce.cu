@@ -34,7 +34,9 @@ __device__ __forceinline__ Comp comp_merge(Comp a, Comp b)
     return r;
 }
 
-template <typename T, int D>
+// SPLIT: the state is in the colour-split layout (a point and its neighbours
+// are of opposite colours: the neighbours sit in the other half).
+template <typename T, int D, bool SPLIT>
 __global__ void __launch_bounds__(256) invariants_kernel(const vec2_t<T>* __restrict__ pq,
                                                          const vec2_t<T>* __restrict__ uv,
                                                          int64_t N, int64_t M, InvParams p,
@@ -42,28 +44,34 @@ __global__ void __launch_bounds__(256) invariants_kernel(const vec2_t<T>* __rest
 {
     Comp e{0, 0}, sc{0, 0}, ms{0, 0};
     const T* u = reinterpret_cast<const T*>(uv);
+    const int64_t half = M >> 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const vec2_t<T> a = pq[i];
-        const vec2_t<T> b = uv[i];
-        const double P = (double)a.x, Q = (double)a.y, U = (double)b.x, V = (double)b.y;
-        // forward neighbours along each axis (periodic)
+        // forward neighbours along each axis (periodic), and the point's colour
         int64_t up[D];
+        int par = 0;
         {
             int64_t rem = i, st = 1;
             for (int ax = D - 1; ax >= 0; --ax) {
                 const int64_t coord = rem % N;
                 rem /= N;
+                par += (int)(coord & 1);
                 up[ax] = (coord == N - 1) ? i - (N - 1) * st : i + st;
                 st *= N;
             }
         }
+        const int64_t own = SPLIT ? ((par & 1) ? half : 0) + (i >> 1) : i;
+        const int64_t oth = SPLIT ? ((par & 1) ? 0 : half) : 0;
+        const vec2_t<T> a = pq[own];
+        const vec2_t<T> b = uv[own];
+        const double P = (double)a.x, Q = (double)a.y, U = (double)b.x, V = (double)b.y;
         double gp = 0.0, gu = 0.0;
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {
-            const vec2_t<T> c = pq[up[ax]];
+            const int64_t k = SPLIT ? oth + (up[ax] >> 1) : up[ax];
+            const vec2_t<T> c = pq[k];
             const double dp = (double)c.x - P, dq = (double)c.y - Q;
-            const double du = (double)u[2 * up[ax]] - U;
+            const double du = (double)u[2 * k] - U;
             gp += dp * dp + dq * dq;
             gu += du * du;
         }
@@ -129,12 +137,13 @@ template <typename T>
 int launch_invariants(const Grid& g, const vec2_t<T>* pq, const vec2_t<T>* uv, const InvParams& p,
                       double* partials, int nblocks, double* out3, cudaStream_t stream)
 {
-    if (g.dim == 1)
-        invariants_kernel<T, 1><<<nblocks, 256, 0, stream>>>(pq, uv, g.N, g.M, p, partials);
-    else if (g.dim == 2)
-        invariants_kernel<T, 2><<<nblocks, 256, 0, stream>>>(pq, uv, g.N, g.M, p, partials);
-    else
-        invariants_kernel<T, 3><<<nblocks, 256, 0, stream>>>(pq, uv, g.N, g.M, p, partials);
+#define KGS_INV(DD)                                                                              \
+    if (g.split) invariants_kernel<T, DD, true><<<nblocks, 256, 0, stream>>>(pq, uv, g.N, g.M, p, partials); \
+    else invariants_kernel<T, DD, false><<<nblocks, 256, 0, stream>>>(pq, uv, g.N, g.M, p, partials);
+    if (g.dim == 1) { KGS_INV(1) }
+    else if (g.dim == 2) { KGS_INV(2) }
+    else { KGS_INV(3) }
+#undef KGS_INV
     invariants_finalize<<<1, 256, 0, stream>>>(partials, nblocks, p.hd, out3);
     return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }

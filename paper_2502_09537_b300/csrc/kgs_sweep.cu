@@ -63,19 +63,23 @@ __device__ __forceinline__ int64_t colour_point(int64_t t, int64_t N, int parity
 }
 
 // beta S_P, beta S_Q and B' S_U over the neighbours nb of colour_point.
+// GLOBAL: the state is the handle's, in HBM in the colour-split layout (the
+// neighbours sit in the other colour's half, from pq + oth); otherwise it is in
+// shared memory in natural order (oth = 0, positions are linear indices).
 template <typename T, int D, bool GLOBAL>
 __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t<T>* uv,
-                                               const int64_t nb[2 * D], const Coef<T>& c,
+                                               const int64_t nb[2 * D], int64_t oth, const Coef<T>& c,
                                                T& bSP, T& bSQ, T& BSU)
 {
     const T* u = reinterpret_cast<const T*>(uv);
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int n = 0; n < 2 * D; ++n) {
-        const vec2_t<T> b = GLOBAL ? __ldg(&pq[nb[n]]) : pq[nb[n]];
+        const int64_t k = GLOBAL ? oth + (nb[n] >> 1) : nb[n];
+        const vec2_t<T> b = GLOBAL ? __ldg(&pq[k]) : pq[k];
         p[n] = b.x;
         q[n] = b.y;
-        w[n] = GLOBAL ? __ldg(&u[2 * nb[n]]) : u[2 * nb[n]];
+        w[n] = GLOBAL ? __ldg(&u[2 * k]) : u[2 * k];
     }
     bSP = nsum_scaled(p, c.beta);
     bSQ = nsum_scaled(q, c.beta);
@@ -84,17 +88,19 @@ __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t
 
 template <typename T, int D, int MODE, bool GLOBAL>
 __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int64_t t, int64_t N,
-                                              int parity, const Coef<T>& c)
+                                              int64_t half, int parity, const Coef<T>& c)
 {
     int64_t nb[2 * D];
     const int64_t i = colour_point<D>(t, N, parity, nb);
+    const int64_t own = GLOBAL ? (parity ? half : 0) + (i >> 1) : i;
+    const int64_t oth = GLOBAL ? (parity ? 0 : half) : 0;
     T bSP, bSQ, BSU;
-    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, c, bSP, bSQ, BSU);
-    vec2_t<T> a = pq[i];
-    vec2_t<T> b = uv[i];
+    neighbour_sums<T, D, GLOBAL>(pq, uv, nb, oth, c, bSP, bSQ, BSU);
+    vec2_t<T> a = pq[own];
+    vec2_t<T> b = uv[own];
     update_point<T, D, MODE>(c, bSP, bSQ, BSU, a.x, a.y, b.x, b.y);
-    pq[i] = a;
-    uv[i] = b;
+    pq[own] = a;
+    uv[own] = b;
 }
 
 // One launch per colour pass.  The launch grid carries the row coordinates
@@ -142,20 +148,25 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
         nb[4] = km;
         nb[5] = kp;
     }
+    // colour-split layout: this colour's half from pq + own, the other's from pq + oth
+    const I half = (D == 1 ? n : (D == 2 ? n * n : n * n * n)) >> 1;
+    const I own = (parity ? half : 0) + (i >> 1);
+    const I oth = parity ? 0 : half;
     const T* u = reinterpret_cast<const T*>(uv);
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
-        const vec2_t<T> b = __ldg(&pq[nb[m]]);
+        const I k = oth + (nb[m] >> 1);
+        const vec2_t<T> b = __ldg(&pq[k]);
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = __ldg(&u[2 * nb[m]]);
+        w[m] = __ldg(&u[2 * k]);
     }
-    vec2_t<T> a = pq[i];
-    vec2_t<T> b = uv[i];
+    vec2_t<T> a = pq[own];
+    vec2_t<T> b = uv[own];
     update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x, a.y, b.x, b.y);
-    pq[i] = a;
-    uv[i] = b;
+    pq[own] = a;
+    uv[own] = b;
 }
 
 // Persistent variant: a grid sized so that every thread gets nearly the same
@@ -169,7 +180,7 @@ __global__ void __launch_bounds__(256) pass_persistent_kernel(vec2_t<T>* pq, vec
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride)
-        colour_update<T, D, MODE, true>(pq, uv, t, N, parity, c);
+        colour_update<T, D, MODE, true>(pq, uv, t, N, half, parity, c);
 }
 
 template <typename T, int D, int MODE>
@@ -177,7 +188,7 @@ __device__ __forceinline__ void smem_pass(vec2_t<T>* pq, vec2_t<T>* uv, int64_t 
                                           int parity, const Coef<T>& c)
 {
     for (int64_t t = threadIdx.x; t < half; t += blockDim.x)
-        colour_update<T, D, MODE, false>(pq, uv, t, N, parity, c);
+        colour_update<T, D, MODE, false>(pq, uv, t, N, half, parity, c);
     __syncthreads();
 }
 
@@ -188,12 +199,14 @@ __global__ void __launch_bounds__(1024) smem_run_kernel(vec2_t<T>* pq, vec2_t<T>
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec2_t<T>* spq = reinterpret_cast<vec2_t<T>*>(smem_raw);
     vec2_t<T>* suv = spq + M;
+    const int64_t half = M >> 1;
+    // natural order in shared memory, the colour-split layout in HBM
     for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
-        spq[i] = pq[i];
-        suv[i] = uv[i];
+        const int64_t j = split_pos(i, D, N, half);
+        spq[i] = pq[j];
+        suv[i] = uv[j];
     }
     __syncthreads();
-    const int64_t half = M >> 1;
     const int red = red_parity(D), black = red ^ 1;
     smem_pass<T, D, RED_BASE>(spq, suv, N, half, red, c);
     for (int64_t n = 1; n < nsteps; ++n) {
@@ -203,8 +216,9 @@ __global__ void __launch_bounds__(1024) smem_run_kernel(vec2_t<T>* pq, vec2_t<T>
     smem_pass<T, D, BLACK_FUSED>(spq, suv, N, half, black, c);
     smem_pass<T, D, RED_ADJ>(spq, suv, N, half, red, c);
     for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
-        pq[i] = spq[i];
-        uv[i] = suv[i];
+        const int64_t j = split_pos(i, D, N, half);
+        pq[j] = spq[i];
+        uv[j] = suv[i];
     }
 }
 
