@@ -68,7 +68,7 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 # DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
 # ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
 # the kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("3d", "fp32"): 2.1518e9 + 1.0394e9}   # pass_kernel_fp32_kgs3d_N512.md
+NCU_TRAFFIC = {}  # filled from the current kernels' captures (profiles/) as they are taken
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), 148 SMs, 2032 MHz maximum SM

@@ -563,8 +563,8 @@ int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* 
         }
         void* dst = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
-                    ? launch_pack<double>(h->M, (double2*)dst, f & 1, d, s, h->dim, h->N)
-                    : launch_pack<float>(h->M, (float2*)dst, f & 1, d, s, h->dim, h->N);
+                    ? launch_pack<double>(h->M, (double2*)dst, f & 1, d, s, h->dim, h->N, f >= 2)
+                    : launch_pack<float>(h->M, (float2*)dst, f & 1, d, s, h->dim, h->N, f >= 2);
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "pack launch");
         h->launches += n;
     }
@@ -592,8 +592,8 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int 
         double* d = (where == KGS_HOST) ? h->stage : dst[f];
         const void* src = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
-                    ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s, h->dim, h->N)
-                    : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s, h->dim, h->N);
+                    ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s, h->dim, h->N, f >= 2)
+                    : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s, h->dim, h->N, f >= 2);
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "unpack launch");
         h->launches += n;
         if (where == KGS_HOST) {

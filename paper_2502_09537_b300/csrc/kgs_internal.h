@@ -23,12 +23,14 @@ struct Grid {
     bool split = false;  // state in the colour-split layout (below)
 };
 
-// Colour-split state layout (a handle's vec2 arrays (P,Q) and (U,V)): the
-// points of even coordinate sum first, then those of odd coordinate sum, each
-// colour in natural (C) order; with N even, point i sits at
-// (parity(i) ? M/2 : 0) + (i >> 1).  A colour pass then reads and writes its
-// own colour's contiguous half and gathers the other half's neighbours with
-// consecutive threads on consecutive elements.
+// Colour-split state layout (a handle's state): the points of even coordinate
+// sum first, then those of odd coordinate sum, each colour in natural (C)
+// order; with N even, point i sits at position (parity(i) ? M/2 : 0) + (i >> 1).
+// (P,Q) is a vec2 array in that order; the (U,V) buffer holds U for all
+// positions, then V for all positions (planar), so a gather of the other
+// colour's U reads no V.  A colour pass then reads and writes its own colour's
+// contiguous half and gathers the other half's neighbours with consecutive
+// threads on consecutive elements.
 __host__ __device__ __forceinline__ int point_parity(int64_t i, int dim, int64_t N)
 {
     if (dim == 1) return (int)(i & 1);
@@ -86,14 +88,16 @@ int launch_level(int dim, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t*
 
 // Layout conversion (kgs_layout.cu): one float64 field <-> one component of a
 // vec2 array, natural order on the float64 side; dim > 0 puts the vec2 side in
-// the colour-split layout of an N^dim grid.  launch_split_convert: whole (P,Q)
-// and (U,V) arrays between the two layouts (to_split: natural -> split).
+// the colour-split layout of an N^dim grid, planar = the (U,V) buffer's planar
+// form (component comp at comp M + position).  launch_split_convert: whole
+// (P,Q) and (U,V) buffers between natural vec2 order and the colour-split
+// layout (to_split: natural -> split).
 template <typename T>
 int launch_pack(int64_t M, vec2_t<T>* dst, int comp, const double* src, cudaStream_t stream,
-                int dim = 0, int64_t N = 0);
+                int dim = 0, int64_t N = 0, bool planar = false);
 template <typename T>
 int launch_unpack(int64_t M, double* dst, const vec2_t<T>* src, int comp, cudaStream_t stream,
-                  int dim = 0, int64_t N = 0);
+                  int dim = 0, int64_t N = 0, bool planar = false);
 template <typename T>
 int launch_split_convert(const Grid& g, bool to_split, const vec2_t<T>* pq_in, const vec2_t<T>* uv_in,
                          vec2_t<T>* pq_out, vec2_t<T>* uv_out, cudaStream_t stream);

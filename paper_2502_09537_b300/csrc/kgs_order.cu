@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) level_kernel(vec2_t<T>* pq, vec2_t<T>* uv
     const int64_t half = (D == 1 ? N : (D == 2 ? N * N : N * N * N)) >> 1;
     const int par = point_parity(i, D, N);
     const int64_t own = (par ? half : 0) + (i >> 1), oth = par ? 0 : half;
-    const T* u = reinterpret_cast<const T*>(uv);
+    T* u = reinterpret_cast<T*>(uv);  // planar: U at a position, V at 2 half + position
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
@@ -66,14 +66,15 @@ __global__ void __launch_bounds__(256) level_kernel(vec2_t<T>* pq, vec2_t<T>* uv
         const vec2_t<T> b = pq[j];
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = u[2 * j];
+        w[m] = u[j];
     }
     vec2_t<T> a = pq[own];
-    vec2_t<T> b = uv[own];
+    T U = u[own], V = u[2 * half + own];
     update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x,
-                             a.y, b.x, b.y);
+                             a.y, U, V);
     pq[own] = a;
-    uv[own] = b;
+    u[own] = U;
+    u[2 * half + own] = V;
 }
 
 template <int D>

@@ -63,15 +63,17 @@ __global__ void __launch_bounds__(256) invariants_kernel(const vec2_t<T>* __rest
         const int64_t own = SPLIT ? ((par & 1) ? half : 0) + (i >> 1) : i;
         const int64_t oth = SPLIT ? ((par & 1) ? 0 : half) : 0;
         const vec2_t<T> a = pq[own];
-        const vec2_t<T> b = uv[own];
-        const double P = (double)a.x, Q = (double)a.y, U = (double)b.x, V = (double)b.y;
+        // (U,V): planar in the colour-split layout, vec2 otherwise
+        const double P = (double)a.x, Q = (double)a.y;
+        const double U = (double)(SPLIT ? u[own] : u[2 * own]);
+        const double V = (double)(SPLIT ? u[M + own] : u[2 * own + 1]);
         double gp = 0.0, gu = 0.0;
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {
             const int64_t k = SPLIT ? oth + (up[ax] >> 1) : up[ax];
             const vec2_t<T> c = pq[k];
             const double dp = (double)c.x - P, dq = (double)c.y - Q;
-            const double du = (double)u[2 * k] - U;
+            const double du = (double)u[SPLIT ? k : 2 * k] - U;
             gp += dp * dp + dq * dq;
             gu += du * du;
         }

@@ -64,8 +64,9 @@ __device__ __forceinline__ int64_t colour_point(int64_t t, int64_t N, int parity
 
 // beta S_P, beta S_Q and B' S_U over the neighbours nb of colour_point.
 // GLOBAL: the state is the handle's, in HBM in the colour-split layout (the
-// neighbours sit in the other colour's half, from pq + oth); otherwise it is in
-// shared memory in natural order (oth = 0, positions are linear indices).
+// neighbours sit in the other colour's half, from pq + oth; U planar); otherwise
+// it is in shared memory in natural vec2 order (oth = 0, positions are linear
+// indices).
 template <typename T, int D, bool GLOBAL>
 __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t<T>* uv,
                                                const int64_t nb[2 * D], int64_t oth, const Coef<T>& c,
@@ -79,7 +80,7 @@ __device__ __forceinline__ void neighbour_sums(const vec2_t<T>* pq, const vec2_t
         const vec2_t<T> b = GLOBAL ? __ldg(&pq[k]) : pq[k];
         p[n] = b.x;
         q[n] = b.y;
-        w[n] = GLOBAL ? __ldg(&u[2 * k]) : u[2 * k];
+        w[n] = GLOBAL ? __ldg(&u[k]) : u[2 * k];
     }
     bSP = nsum_scaled(p, c.beta);
     bSQ = nsum_scaled(q, c.beta);
@@ -97,10 +98,14 @@ __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int6
     T bSP, bSQ, BSU;
     neighbour_sums<T, D, GLOBAL>(pq, uv, nb, oth, c, bSP, bSQ, BSU);
     vec2_t<T> a = pq[own];
-    vec2_t<T> b = uv[own];
-    update_point<T, D, MODE>(c, bSP, bSQ, BSU, a.x, a.y, b.x, b.y);
+    T* u = reinterpret_cast<T*>(uv);
+    // (U,V): planar in HBM (U at own, V at 2 half + own), vec2 in shared memory
+    const int64_t iu = GLOBAL ? own : 2 * own, iv = GLOBAL ? 2 * half + own : 2 * own + 1;
+    T U = u[iu], V = u[iv];
+    update_point<T, D, MODE>(c, bSP, bSQ, BSU, a.x, a.y, U, V);
     pq[own] = a;
-    uv[own] = b;
+    u[iu] = U;
+    u[iv] = V;
 }
 
 // One launch per colour pass.  The launch grid carries the row coordinates
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     const I half = (D == 1 ? n : (D == 2 ? n * n : n * n * n)) >> 1;
     const I own = (parity ? half : 0) + (i >> 1);
     const I oth = parity ? 0 : half;
-    const T* u = reinterpret_cast<const T*>(uv);
+    T* u = reinterpret_cast<T*>(uv);  // planar: U at a position, V at 2 half + position
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
@@ -160,13 +165,14 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
         const vec2_t<T> b = __ldg(&pq[k]);
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = __ldg(&u[2 * k]);
+        w[m] = __ldg(&u[k]);
     }
     vec2_t<T> a = pq[own];
-    vec2_t<T> b = uv[own];
-    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x, a.y, b.x, b.y);
+    T U = u[own], V = u[2 * half + own];
+    update_point<T, D, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x, a.y, U, V);
     pq[own] = a;
-    uv[own] = b;
+    u[own] = U;
+    u[2 * half + own] = V;
 }
 
 // Persistent variant: a grid sized so that every thread gets nearly the same
@@ -201,10 +207,14 @@ __global__ void __launch_bounds__(1024) smem_run_kernel(vec2_t<T>* pq, vec2_t<T>
     vec2_t<T>* suv = spq + M;
     const int64_t half = M >> 1;
     // natural order in shared memory, the colour-split layout in HBM
+    const T* gu = reinterpret_cast<const T*>(uv);  // planar U, V in HBM
     for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
         const int64_t j = split_pos(i, D, N, half);
         spq[i] = pq[j];
-        suv[i] = uv[j];
+        vec2_t<T> b;
+        b.x = gu[j];
+        b.y = gu[M + j];
+        suv[i] = b;
     }
     __syncthreads();
     const int red = red_parity(D), black = red ^ 1;
@@ -215,10 +225,12 @@ __global__ void __launch_bounds__(1024) smem_run_kernel(vec2_t<T>* pq, vec2_t<T>
     }
     smem_pass<T, D, BLACK_FUSED>(spq, suv, N, half, black, c);
     smem_pass<T, D, RED_ADJ>(spq, suv, N, half, red, c);
+    T* pu = reinterpret_cast<T*>(uv);
     for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
         const int64_t j = split_pos(i, D, N, half);
         pq[j] = spq[i];
-        uv[j] = suv[i];
+        pu[j] = suv[i].x;
+        pu[M + j] = suv[i].y;
     }
 }
 
