@@ -3,7 +3,8 @@
 // kgs_batch_*).
 //
 // Storage: one device arena per batch, of a capacity fixed at creation (the
-// HBM budget), holding every instance's (P,Q) and (U,V) vec2 arrays; instances
+// HBM budget), holding every instance's (P,Q) vec2 array and (U,V) buffer in
+// the colour-split layout of a handle's state (kgs_internal.h); instances
 // are placed first-fit and their space is returned on removal, so a caller can
 // admit new instances as others finish.
 //
@@ -98,25 +99,33 @@ __device__ __forceinline__ I batch_point(I t, int N, int parity, I nb[2 * D])
     return i;
 }
 
+// An instance's state is in the colour-split layout of a handle's
+// (kgs_internal.h): this colour's half from pq + own, the neighbours in the
+// other half, U and V planar in the (U,V) buffer.
 template <typename T, int D, int MODE, typename I>
 __device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int parity)
 {
     I nb[2 * D];
     const I i = batch_point<D, I>(t, in.N, parity, nb);
-    const T* u = reinterpret_cast<const T*>(in.uv);
+    const I half = (I)in.half;
+    const I own = (parity ? half : 0) + (i >> 1);
+    const I oth = parity ? 0 : half;
+    T* u = reinterpret_cast<T*>(in.uv);
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
-        const vec2_t<T> b = __ldg(&in.pq[nb[m]]);
+        const I k = oth + (nb[m] >> 1);
+        const vec2_t<T> b = __ldg(&in.pq[k]);
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = __ldg(&u[2 * nb[m]]);
+        w[m] = __ldg(&u[k]);
     }
-    vec2_t<T> a = in.pq[i];
-    vec2_t<T> b = in.uv[i];
-    update_point<T, D, MODE>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta), nsum_scaled(w, in.coef.Bp), a.x, a.y, b.x, b.y);
-    in.pq[i] = a;
-    in.uv[i] = b;
+    vec2_t<T> a = in.pq[own];
+    T U = u[own], V = u[2 * half + own];
+    update_point<T, D, MODE>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta), nsum_scaled(w, in.coef.Bp), a.x, a.y, U, V);
+    in.pq[own] = a;
+    u[own] = U;
+    u[2 * half + own] = V;
 }
 
 // Pass g (colour: red for even g) of the instances of one list (one precision
@@ -637,10 +646,10 @@ int kgs_batch_set_state(kgs_batch_handle b, int64_t id, const double* P, const d
         int n;
         if (h.precision == 64) {
             double2* dst = reinterpret_cast<double2*>(base) + (f < 2 ? 0 : h.M);
-            n = launch_pack<double>(h.M, dst, f & 1, d, s);
+            n = launch_pack<double>(h.M, dst, f & 1, d, s, h.dim, h.N, f >= 2);
         } else {
             float2* dst = reinterpret_cast<float2*>(base) + (f < 2 ? 0 : h.M);
-            n = launch_pack<float>(h.M, dst, f & 1, d, s);
+            n = launch_pack<float>(h.M, dst, f & 1, d, s, h.dim, h.N, f >= 2);
         }
         if (n < 0) return bcuda(b, cudaGetLastError(), "pack launch");
         b->launches += n;
@@ -678,10 +687,10 @@ int kgs_batch_get_state(kgs_batch_handle b, int64_t id, double* P, double* Q, do
         int n;
         if (h.precision == 64) {
             const double2* src = reinterpret_cast<const double2*>(base) + (f < 2 ? 0 : h.M);
-            n = launch_unpack<double>(h.M, d, src, f & 1, s);
+            n = launch_unpack<double>(h.M, d, src, f & 1, s, h.dim, h.N, f >= 2);
         } else {
             const float2* src = reinterpret_cast<const float2*>(base) + (f < 2 ? 0 : h.M);
-            n = launch_unpack<float>(h.M, d, src, f & 1, s);
+            n = launch_unpack<float>(h.M, d, src, f & 1, s, h.dim, h.N, f >= 2);
         }
         if (n < 0) return bcuda(b, cudaGetLastError(), "unpack launch");
         b->launches += n;
@@ -745,6 +754,7 @@ int kgs_batch_invariants(kgs_batch_handle b, int64_t id, double* out3, void* str
     p.hd = 1.0;
     for (int a = 0; a < h.dim; ++a) p.hd *= hh;
     Grid g{h.dim, h.N, h.M};
+    g.split = true;
     const int nb = invariants_blocks(h.M);
     const char* base = b->arena + h.off;
     int n = (h.precision == 64)
