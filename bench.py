@@ -352,7 +352,8 @@ def run_serve(args):
             for k in range(args.warmup + args.steps):
                 reqs = serve.poisson_requests(args.rate, args.requests, seed=SEED_SERVE + 1000 * rank + k,
                                               step_range=(100, args.max_steps))
-                srv = serve.Server(budget, quantum=100, stream=stream, keep_state=True)
+                srv = serve.Server(budget, quantum=100, stream=stream, keep_state=True,
+                                   turn_work=args.turn_work)
                 for r in reqs:
                     srv.submit(r)
                 l0 = srv.batch.launch_count
@@ -376,7 +377,7 @@ def run_serve(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "kgs_serve", "rate_per_s": args.rate,
                    "requests_per_step": args.requests, "step_range": [100, args.max_steps],
-                   "budget_bytes": budget, "quantum_steps": 100,
+                   "budget_bytes": budget, "quantum_steps": 100, "turn_work": args.turn_work,
                    "l2": "inputs are built per request on the host (cold)",
                    "parallelism": f"{world} independent server(s), one per GPU"},
         "latency_s": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99)},
@@ -430,6 +431,8 @@ def main():
     ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d", "batch", "serve"])
     ap.add_argument("--rate", type=float, default=50.0, help="serving: request arrival rate (1/s)")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests per timed step")
+    ap.add_argument("--turn-work", type=float, default=5e9,
+                    help="serving: point-updates per turn, shortest remaining work first (0: all)")
     ap.add_argument("--max-steps", type=int, default=1000,
                     help="serving: upper end of the per-request step range (workload: 10000)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])

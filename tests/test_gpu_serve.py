@@ -39,10 +39,11 @@ def solo(req):
         return s.get_state()
 
 
-@pytest.mark.parametrize("budget,slots,quantum", [(1 << 30, 64, 10), (700_000, 3, 7)])
-def test_results_in_the_mix_equal_results_alone(budget, slots, quantum):
+@pytest.mark.parametrize("budget,slots,quantum,turn_work", [(1 << 30, 64, 10, 0.0), (700_000, 3, 7, 0.0),
+                                                              (1 << 30, 64, 10, 2e5)])
+def test_results_in_the_mix_equal_results_alone(budget, slots, quantum, turn_work):
     reqs = make_requests()
-    srv = serve.Server(budget, quantum=quantum, max_slots=slots)
+    srv = serve.Server(budget, quantum=quantum, max_slots=slots, turn_work=turn_work, max_wait=0.5)
     for r in reqs:
         srv.submit(r)
     results = srv.run()
