@@ -588,7 +588,8 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_median": float(np.median(iter_ms)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,

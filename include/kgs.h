@@ -20,7 +20,9 @@
  *
  * Ownership: the library owns every device buffer of a handle (allocated in
  * kgs_create*, freed in kgs_destroy).  Caller buffers passed to kgs_set_state /
- * kgs_get_state are never retained.
+ * kgs_get_state are never retained.  The order in which a handle keeps its
+ * state on the device is the library's own (each colour's points contiguous)
+ * and never seen by callers, who always exchange the layout above.
  *
  * Streams: every `stream` argument is a cudaStream_t passed as void*; NULL is
  * the legacy default stream.  Calls that take device buffers are asynchronous
