@@ -608,7 +608,7 @@ def main():
         "kernel_ms_per_launch": pass_ms,
         "kernel_launches_per_solve": step_launches[0] / args.steps,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline: N = 1 only
         line["cpu_baseline"] = cpu_baseline(work)
     s.close()
     if dist:
