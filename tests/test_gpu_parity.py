@@ -90,8 +90,10 @@ def test_fp64_matches_oracle(orc, case):
 
 
 @pytest.mark.parametrize("dim,N", [(1, 4), (1, 6), (2, 4), (2, 6), (3, 4), (3, 6), (1, 10), (2, 12)])
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5])
 def test_tiny_grids_both_kernels(orc, dim, N, kernel):
+    if kernel == 5 and dim == 1:
+        pytest.skip("the slab kernel needs dim 2 or 3")
     prob = Problem(dim, N, 3.0 + N / 7, 1.1, 0.9, 1.2, 0.8, 0.02)
     st = random_state(prob, 100 + N + dim, 0.7)
     gpu = run_gpu(prob, st, 50, kernel=kernel)
@@ -166,6 +168,22 @@ def test_split_steps_are_bitwise_equal(kernel):
     parts = run_gpu(prob, st, 100, kernel=kernel, splits=[1, 40, 27, 32])
     for x, y in zip(whole, parts):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("dim,N", [(1, 6), (1, 2050), (2, 6), (2, 66), (3, 6), (3, 18), (3, 130)])
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+def test_state_round_trip(dim, N, precision):
+    """set_state then get_state returns the state (rounded to float32 for
+    FP32 state) in the public natural layout: the device's colour-split order
+    is a bijection, undone exactly."""
+    prob = Problem(dim, N, 5.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 200 + N, 0.5)
+    with Solver.from_problem(prob, precision) as s:
+        s.set_state(*copy_state(st))
+        got = s.get_state()
+    for x, y in zip(got, st):
+        want = y if precision == KGS_FP64 else y.astype(np.float32).astype(np.float64)
+        assert np.array_equal(x, want)
 
 
 def test_device_pointer_path_matches_host_path():
