@@ -448,6 +448,10 @@ def main():
     ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block"],
                     help="update order: the checkerboard (Algorithm 3), the lexicographic "
                          "wavefront (Eq. order1) or Algorithm 2's block order (2D, 16 blocks)")
+    ap.add_argument("--order-mode", type=int, default=0,
+                    help="KGS_OPT_ORDER_MODE for a general order: 0 auto, 1 one launch per level "
+                         "(colour-split layout), 2 one persistent launch per step, 3 one launch per "
+                         "level on a natural-order copy")
     ap.add_argument("--steps-per-solve", type=int, default=0,
                     help="DP-AVF2 steps per benchmark step (default: the workload's)")
     ap.add_argument("--grid-n", type=int, default=0,
@@ -499,6 +503,9 @@ def main():
     if args.slab_planes:
         from paper_2502_09537_b300.solver import KGS_OPT_SLAB_PLANES
         s.set_option(KGS_OPT_SLAB_PLANES, args.slab_planes)
+    if args.order_mode:
+        from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
+        s.set_option(KGS_OPT_ORDER_MODE, args.order_mode)
     if args.order != "checkerboard":
         from paper_2502_09537_b300 import orders
         s.set_order(orders.lexicographic(prob.dim, prob.N) if args.order == "lex"
@@ -594,6 +601,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
                    "threads": args.threads or 256, "kernel": args.kernel, "order": args.order,
+                   "order_mode": args.order_mode,
                    "slab_planes": args.slab_planes,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,

@@ -52,7 +52,9 @@ extern "C" {
 #define KGS_ERR_OOM      -3  /* device allocation failed */
 #define KGS_ERR_CUDA     -4  /* a CUDA call failed (also: no usable device) */
 #define KGS_ERR_STATE    -5  /* no state set yet */
-#define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out */
+#define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out (a grid barrier of the persistent
+                               order launch did not complete within 2 s); the handle's state is
+                               lost and every later call on the handle returns this status */
 #define KGS_ERR_RANGE    -7  /* size beyond what the call supports */
 
 /* memory kind of caller buffers */
@@ -78,6 +80,20 @@ extern "C" {
 #define KGS_OPT_TILE_LX      7  /* tile kernel: axis-0 planes per CTA */
 #define KGS_OPT_TILE_PASSES  8  /* tile kernel: colour passes per launch (= halo width), 1..8 */
 #define KGS_OPT_TILE_THREADS 9  /* tile kernel: threads per CTA (64, 128, 256, 512, 1024) */
+#define KGS_OPT_ORDER_MODE  11  /* update orders (kgs_set_order): 0 auto (default: mode 3, or
+                                   mode 1 if the second state buffer cannot be allocated), 1 one
+                                   launch per level on the handle's state layout (a step captured
+                                   in a CUDA graph), 2 every level of a step in one cooperative
+                                   persistent launch with a grid barrier after each level
+                                   (bounded: see KGS_ERR_TIMEOUT; kgs_step then waits for the
+                                   device before returning), 3 one launch per level on a natural-
+                                   order copy of the state (a second state buffer, allocated on
+                                   first use; each kgs_step call converts into it and back).  All
+                                   compute bitwise the same state. */
+#define KGS_OPT_TEST_BARRIER_STALL 12  /* test hook: n > 0 makes every grid barrier of the
+                                   persistent order launch wait for n CTAs that do not exist, so
+                                   it times out (after 2 s) and kgs_step returns KGS_ERR_TIMEOUT;
+                                   0 (default) off.  For testing the timeout path only. */
 #define KGS_OPT_SLAB_PLANES 10  /* slab kernel: axis-0 planes per slab, 1 .. N; 0 (default) picks
                                    about a quarter of the L2 cache's bytes per slab.  A step's
                                    black pass runs slab by slab and each slab's red pass follows
@@ -152,7 +168,8 @@ int kgs_step(kgs_handle h, int64_t nsteps, void* stream);
  * kgs_set_order: make `order` (N^d int64, host; copied) the handle's update
  * order from the next kgs_step on; NULL restores the checkerboard.  The
  * handle keeps the points sorted by level on the device (8 bytes per point);
- * the kernel options (KGS_OPT_*) apply to the checkerboard only.  Waits for
+ * the colour-pass kernel options apply to the checkerboard only and
+ * KGS_OPT_ORDER_MODE to the other orders.  Waits for
  * the device to finish queued work first.  Returns KGS_OK, KGS_ERR_ARG (not
  * a permutation; the handle's order is unchanged), KGS_ERR_OOM (host or
  * device memory) or KGS_ERR_CUDA.
@@ -184,7 +201,8 @@ int kgs_mass(kgs_handle h, double* M);
 int kgs_set_tau(kgs_handle h, double tau);
 
 /* Tuning options (KGS_OPT_*); values out of range return KGS_ERR_ARG.  None
- * changes results: every kernel variant computes bitwise the same state. */
+ * changes results: every kernel variant computes bitwise the same state (the
+ * test hook KGS_OPT_TEST_BARRIER_STALL makes stepping fail on purpose). */
 int kgs_set_option(kgs_handle h, int option, int64_t value);
 
 /* Number of kernels this handle has launched so far (graph replays count

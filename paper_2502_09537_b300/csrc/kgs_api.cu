@@ -8,6 +8,7 @@
 // kgs_point.cuh): small grids as one shared-memory resident launch, larger
 // ones as one launch per pass, the repeated (BLACK_FUSED, RED_FUSED) pairs
 // replayed from a captured CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -72,6 +73,13 @@ struct kgs_solver {
     std::vector<int64_t> olevels;
     cudaGraphExec_t ograph = nullptr;  // one step of the order, captured
     int ograph_buf = -1;
+    bool ograph_split = true;          // the layout the order graph was captured for
+    int64_t* olevels_dev = nullptr;    // level offsets on the device (persistent launches)
+    int64_t omax_level = 0;            // points in the largest level
+    OrderBarrier* obar = nullptr;      // grid barrier of the persistent launches
+    int opt_order_mode = 0;            // 0 auto, 1 levels on the split layout, 2 persistent, 3 levels on natural order
+    int opt_stall = 0;                 // test hook: phantom CTAs every barrier waits for
+    bool timed_out = false;            // a bounded device wait ran out: the state is lost
 };
 
 namespace {
@@ -101,6 +109,8 @@ int cuda_fail(kgs_solver* h, cudaError_t e, const char* what)
 int check_handle(kgs_solver* h)
 {
     if (!h) return fail(KGS_ERR_ARG, "NULL handle");
+    if (h->timed_out)
+        return fail(KGS_ERR_TIMEOUT, "handle is in error state after a device wait timed out");
     if (h->sticky)
         return fail(KGS_ERR_CUDA, "handle is in error state after: %s",
                     cudaGetErrorString((cudaError_t)h->sticky));
@@ -180,7 +190,7 @@ int ensure_tile_buffers(kgs_solver* h)
         h->pqb[1] = nullptr;
         h->uvb[1] = nullptr;
         return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA,
-                    "second state buffer for the tile kernel (%zu bytes): %s", 2 * bytes,
+                    "second state buffer (%zu bytes): %s", 2 * bytes,
                     cudaGetErrorString(e));
     }
     return 0;
@@ -292,7 +302,7 @@ int ensure_graph(kgs_solver* h)
 // One DP-AVF2 step in the handle's order: the base half over the levels in
 // increasing order, the adjoint half in decreasing order.
 template <typename T>
-int order_step(kgs_solver* h, cudaStream_t s)
+int order_step(kgs_solver* h, bool split, cudaStream_t s)
 {
     const Coef<T>* c;
     if constexpr (sizeof(T) == 8) c = &h->cd;
@@ -305,7 +315,7 @@ int order_step(kgs_solver* h, cudaStream_t s)
             const int64_t l = pass == 0 ? k : nl - 1 - k;
             const int64_t o = h->olevels[(size_t)l], n = h->olevels[(size_t)l + 1] - o;
             const int r = launch_level<T>(h->dim, pass == 0 ? RED_BASE : RED_ADJ, pq, uv, h->olist + o, n,
-                                          h->N, *c, s);
+                                          h->N, *c, split, s);
             if (r < 0) return -1;
             h->launches += r;
         }
@@ -314,10 +324,92 @@ int order_step(kgs_solver* h, cudaStream_t s)
 }
 
 template <typename T>
+int step_in_order_persistent(kgs_solver* h, int64_t nsteps, cudaStream_t s)
+{
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    const int64_t nl = (int64_t)h->olevels.size() - 1;
+    cudaError_t e = cudaMemsetAsync(h->obar, 0, sizeof(OrderBarrier), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "barrier reset");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        // count and generation restart each launch; the error flag is kept
+        e = cudaMemsetAsync(h->obar, 0, 2 * sizeof(unsigned), s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "barrier reset");
+        if (launch_level_persistent<T>(h->dim, (vec2_t<T>*)h->pqb[h->cur], (vec2_t<T>*)h->uvb[h->cur],
+                                       h->olist, h->olevels_dev, nl, h->omax_level, h->N, *c, h->obar,
+                                       h->opt_stall, s) < 0)
+            return cuda_fail(h, cudaGetLastError(), "persistent order launch");
+        h->launches += 1;
+    }
+    int err = 0;
+    e = cudaMemcpyAsync(&err, &h->obar->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "barrier status");
+    if (err) {
+        h->timed_out = true;
+        return fail(KGS_ERR_TIMEOUT, "a level barrier of the persistent order launch timed out");
+    }
+    return KGS_OK;
+}
+
+// Levels on natural vec2 order: convert the state into the other buffer pair
+// (to_natural) or back into the colour-split layout, and make that pair current.
+template <typename T>
+int order_convert(kgs_solver* h, bool to_natural, cudaStream_t s)
+{
+    if (to_natural) {
+        const int st = ensure_tile_buffers(h);
+        if (st) return st;
+    }
+    const int o = h->cur ^ 1;
+    if (launch_split_convert<T>(grid_of(h), !to_natural, (const vec2_t<T>*)h->pqb[h->cur],
+                                (const vec2_t<T>*)h->uvb[h->cur], (vec2_t<T>*)h->pqb[o], (vec2_t<T>*)h->uvb[o],
+                                s) < 0)
+        return cuda_fail(h, cudaGetLastError(), "layout conversion");
+    h->launches += 1;
+    h->cur = o;
+    return KGS_OK;
+}
+
+template <typename T>
+int step_in_order_levels(kgs_solver* h, int64_t nsteps, bool split, cudaStream_t s);
+
+template <typename T>
 int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 {
+    if (h->opt_order_mode == 2) return step_in_order_persistent<T>(h, nsteps, s);
+    // natural order suits the level schedules better: a level's points (an
+    // anti-diagonal of the lexicographic order, say) find their neighbours
+    // along the last axis in the cache sectors of their own values
+    bool natural = h->opt_order_mode == 3;
+    if (h->opt_order_mode == 0) {
+        // without room for the copy, fall back to the levels on the split
+        // layout, leaving the caller's last-error record as it was
+        const int saved = g_last_status;
+        char msg[sizeof g_last_error];
+        memcpy(msg, g_last_error, sizeof msg);
+        natural = ensure_tile_buffers(h) == 0;
+        if (!natural) {
+            g_last_status = saved;
+            memcpy(g_last_error, msg, sizeof msg);
+        }
+    }
+    if (natural) {
+        int st = order_convert<T>(h, true, s);
+        if (st) return st;
+        st = step_in_order_levels<T>(h, nsteps, false, s);
+        const int st2 = order_convert<T>(h, false, s);
+        return st ? st : st2;
+    }
+    return step_in_order_levels<T>(h, nsteps, true, s);
+}
+
+template <typename T>
+int step_in_order_levels(kgs_solver* h, int64_t nsteps, bool split, cudaStream_t s)
+{
     if (h->opt_graph && nsteps >= 2) {
-        if (!(h->ograph && h->ograph_buf == h->cur)) {
+        if (!(h->ograph && h->ograph_buf == h->cur && h->ograph_split == split)) {
             if (h->ograph) {
                 cudaGraphExecDestroy(h->ograph);
                 h->ograph = nullptr;
@@ -329,7 +421,7 @@ int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
             cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
             const int64_t l0 = h->launches;
-            const int r = order_step<T>(h, h->capture_stream);
+            const int r = order_step<T>(h, split, h->capture_stream);
             h->launches = l0;
             cudaGraph_t graph = nullptr;
             e = cudaStreamEndCapture(h->capture_stream, &graph);
@@ -345,6 +437,7 @@ int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
                 return cuda_fail(h, e, "cudaGraphInstantiate");
             }
             h->ograph_buf = h->cur;
+            h->ograph_split = split;
         }
         int64_t per = 0;
         for (size_t l = 0; l + 1 < h->olevels.size(); ++l) per += h->olevels[l + 1] > h->olevels[l];
@@ -356,7 +449,7 @@ int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
         return KGS_OK;
     }
     for (int64_t k = 0; k < nsteps; ++k)
-        if (order_step<T>(h, s)) return cuda_fail(h, cudaGetLastError(), "order level launch");
+        if (order_step<T>(h, split, s)) return cuda_fail(h, cudaGetLastError(), "order level launch");
     return KGS_OK;
 }
 
@@ -442,7 +535,11 @@ void free_all(kgs_solver* h)
 {
     drop_graph(h);
     cudaFree(h->olist);
+    cudaFree(h->olevels_dev);
+    cudaFree(h->obar);
     h->olist = nullptr;
+    h->olevels_dev = nullptr;
+    h->obar = nullptr;
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->pqb[b]);
@@ -649,7 +746,9 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     drop_graph(h);
     if (!order) {
         cudaFree(h->olist);
+        cudaFree(h->olevels_dev);
         h->olist = nullptr;
+        h->olevels_dev = nullptr;
         h->olevels.clear();
         return KGS_OK;
     }
@@ -667,6 +766,18 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     }
     e = cudaMemcpy(h->olist, list.data(), (size_t)h->M * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "order upload");
+    cudaFree(h->olevels_dev);
+    h->olevels_dev = nullptr;
+    e = cudaMalloc(&h->olevels_dev, off.size() * sizeof(int64_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->olevels_dev, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h->obar) e = cudaMalloc(&h->obar, sizeof(OrderBarrier));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KGS_ERR_OOM, "device memory for the order's level offsets");
+    }
+    h->omax_level = 0;
+    for (size_t l = 0; l + 1 < off.size(); ++l) h->omax_level = std::max(h->omax_level, off[l + 1] - off[l]);
     h->olevels.swap(off);
     return KGS_OK;
 }
@@ -788,6 +899,14 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     case KGS_OPT_GRAPH:
         if (value < 0 || value > 1) return fail(KGS_ERR_ARG, "KGS_OPT_GRAPH takes 0 or 1");
         h->opt_graph = (int)value;
+        return KGS_OK;
+    case KGS_OPT_ORDER_MODE:
+        if (value < 0 || value > 3) return fail(KGS_ERR_ARG, "KGS_OPT_ORDER_MODE takes 0 to 3");
+        h->opt_order_mode = (int)value;
+        return KGS_OK;
+    case KGS_OPT_TEST_BARRIER_STALL:
+        if (value < 0 || value > 1024) return fail(KGS_ERR_ARG, "KGS_OPT_TEST_BARRIER_STALL takes 0 to 1024");
+        h->opt_stall = (int)value;
         return KGS_OK;
     case KGS_OPT_SLAB_PLANES:
         if (value < 0 || value > h->N) return fail(KGS_ERR_ARG, "KGS_OPT_SLAB_PLANES takes 0 to N");

@@ -76,15 +76,33 @@ int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<
 // Update orders (kgs_order.cu).  order_schedule: level of every point of a
 // permutation `order` of the N^dim grid (returns 0, -1 if order is not a
 // permutation, -3 if host memory ran out).  order_lists: the points sorted by
-// level (stable in order position) and the level offsets (nlevels + 1).
+// level (stable in order position), as packed coordinates (the last axis in
+// the lowest bits, 63 / 31 / 21 bits per axis in 1 / 2 / 3 dimensions), and
+// the level offsets (nlevels + 1).
 // launch_level: one level's points, MODE RED_BASE (base half) or RED_ADJ
-// (adjoint half); returns 1, 0 for an empty level, -1 if the launch failed.
+// (adjoint half), on the colour-split layout (split) or on natural vec2 order;
+// returns 1, 0 for an empty level, -1 if the launch failed.
 int order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels);
 int order_lists(int dim, int64_t N, const int64_t* order, std::vector<int64_t>& list,
                 std::vector<int64_t>& offsets);
 template <typename T>
 int launch_level(int dim, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t* list, int64_t count,
-                 int64_t N, const Coef<T>& c, cudaStream_t s);
+                 int64_t N, const Coef<T>& c, bool split, cudaStream_t s);
+// launch_level_persistent: one whole step (base half up the levels, adjoint
+// half down) in one cooperative launch of enough CTAs for the largest level
+// (at most all co-resident CTAs), a bounded grid barrier after each level;
+// offsets on the device (nlevels + 1); bar is zeroed on the stream first and
+// bar->err is 1 afterwards if a barrier timed out.  extra > 0 makes every
+// barrier wait for that many CTAs that do not exist (tests the timeout).
+// Returns 1, or -1 if the launch failed.
+struct OrderBarrier {
+    unsigned count, gen;
+    int err, pad;
+};
+template <typename T>
+int launch_level_persistent(int dim, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t* list,
+                            const int64_t* offsets, int64_t nlevels, int64_t max_level, int64_t N,
+                            const Coef<T>& c, OrderBarrier* bar, int extra, cudaStream_t s);
 
 // Layout conversion (kgs_layout.cu): one float64 field <-> one component of a
 // vec2 array, natural order on the float64 side; dim > 0 puts the vec2 side in

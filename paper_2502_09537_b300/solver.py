@@ -33,6 +33,9 @@ KGS_OPT_TILE_LX = 7
 KGS_OPT_TILE_PASSES = 8
 KGS_OPT_TILE_THREADS = 9
 KGS_OPT_SLAB_PLANES = 10
+KGS_OPT_ORDER_MODE = 11
+KGS_OPT_TEST_BARRIER_STALL = 12
+KGS_ERR_TIMEOUT = -6
 
 # Every function the header declares, with its ctypes signature.
 _c_int64 = ctypes.c_int64

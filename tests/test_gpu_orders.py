@@ -127,3 +127,56 @@ def test_reset_and_bad_orders():
         assert s.order_levels() == 2
         s.step(5)
         assert _bitwise(s.get_state(), ref)
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+@pytest.mark.parametrize("name,dim,N", [("lexicographic", 2, 24), ("lexicographic", 3, 8),
+                                        ("random", 2, 14), ("block_split", 2, 26)])
+def test_persistent_levels_are_bitwise_the_per_level_launches(name, dim, N, precision):
+    """KGS_OPT_ORDER_MODE 2 (all levels of a step in one cooperative launch,
+    a grid barrier after each level), 1 (one launch per level) and 3 (one
+    launch per level on natural order) compute bitwise the same state; so does
+    the automatic choice."""
+    from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
+    prob = Problem(dim, N, 10.0, 1.0, 0.8, 1.1, 0.9, 0.01)
+    st = random_state(prob, 2502_09537 + 110 + N)
+    order = {"lexicographic": orders.lexicographic(dim, N),
+             "random": orders.random_order(dim, N, 2502_09537 + 111),
+             "block_split": orders.block_split_2d(N, 4) if dim == 2 else None}[name]
+    out = {}
+    for mode in (1, 2, 3, 0):
+        with Solver.from_problem(prob, precision) as s:
+            s.set_option(KGS_OPT_ORDER_MODE, mode)
+            s.set_state(*_copy(st))
+            s.set_order(order)
+            s.step(7)
+            s.step(5)
+            out[mode] = s.get_state()
+    assert _bitwise(out[1], out[2]) and _bitwise(out[1], out[3]) and _bitwise(out[1], out[0])
+
+
+def test_barrier_timeout_is_reported_and_the_context_survives():
+    """A grid barrier that cannot complete (the test hook makes it wait for a
+    CTA that does not exist) gives up after its 2 s bound: kgs_step returns
+    KGS_ERR_TIMEOUT, the handle refuses further work, and the device stays
+    usable for a new handle."""
+    from paper_2502_09537_b300.solver import (KGS_ERR_TIMEOUT, KGS_OPT_ORDER_MODE,
+                                              KGS_OPT_TEST_BARRIER_STALL)
+    prob = Problem(2, 16, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 120)
+    with Solver.from_problem(prob) as s:
+        s.set_state(*_copy(st))
+        s.set_order(orders.lexicographic(2, 16))
+        s.set_option(KGS_OPT_ORDER_MODE, 2)
+        s.set_option(KGS_OPT_TEST_BARRIER_STALL, 1)
+        with pytest.raises(KGSError) as ei:
+            s.step(1)
+        assert ei.value.status == KGS_ERR_TIMEOUT
+        with pytest.raises(KGSError) as ei:
+            s.get_state()
+        assert ei.value.status == KGS_ERR_TIMEOUT
+    ref, _ = _gpu(prob, st, orders.lexicographic(2, 16), [3])
+    want = _copy(st)
+    from oracle import steps_order
+    steps_order(prob, *want, orders.lexicographic(2, 16), 3)
+    assert _rel(ref, want) <= FP64_BAR
