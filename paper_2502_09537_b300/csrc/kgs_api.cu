@@ -614,7 +614,7 @@ kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kap
     compute_coef(h);
     const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
     const size_t state_bytes = (size_t)h->M * elem;
-    h->nblocks = invariants_blocks(h->M);
+    h->nblocks = invariants_blocks(h->dim, h->N);
     cudaError_t ea = cudaMalloc(&h->pqb[0], state_bytes);
     if (ea == cudaSuccess) ea = cudaMalloc(&h->uvb[0], state_bytes);
     if (ea == cudaSuccess) ea = cudaMalloc(&h->stage, (size_t)h->M * sizeof(double));
@@ -800,14 +800,7 @@ int kgs_invariants(kgs_handle h, double* out3, void* stream)
     DeviceGuard guard(h->device);
     if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    InvParams p;
-    p.kappa1 = h->kappa1;
-    p.kappa2 = h->kappa2;
-    p.mu = h->mu;
-    p.gamma = h->gamma;
-    p.inv_h2 = 1.0 / (h->h * h->h);
-    p.hd = 1.0;
-    for (int a = 0; a < h->dim; ++a) p.hd *= h->h;
+    const InvParams p = make_inv_params(h->dim, h->h, h->kappa1, h->kappa2, h->mu, h->gamma);
     int n = (h->precision == 64)
                 ? launch_invariants<double>(grid_of(h), (const double2*)h->pqb[h->cur],
                                             (const double2*)h->uvb[h->cur], p, h->partials,

@@ -535,7 +535,7 @@ kgs_batch_handle kgs_batch_create(int device, int64_t capacity_bytes)
     b->capacity = ((size_t)capacity_bytes + 255) & ~(size_t)255;
     e = cudaMalloc(&b->arena, b->capacity);
     if (e == cudaSuccess) {
-        b->scratch_blocks = invariants_blocks((int64_t)1 << 40);
+        b->scratch_blocks = invariants_blocks(3, (int64_t)1 << 20);
         e = cudaMalloc(&b->scratch, (size_t)b->scratch_blocks * 3 * sizeof(double));
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->out_dev, 3 * sizeof(double));
@@ -744,18 +744,10 @@ int kgs_batch_invariants(kgs_batch_handle b, int64_t id, double* out3, void* str
     if (!h.state_set) return bfail(KGS_ERR_STATE, "instance has no state");
     BatchDevGuard guard(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    InvParams p;
-    const double hh = h.L / (double)h.N;
-    p.kappa1 = h.kappa1;
-    p.kappa2 = h.kappa2;
-    p.mu = h.mu;
-    p.gamma = h.gamma;
-    p.inv_h2 = 1.0 / (hh * hh);
-    p.hd = 1.0;
-    for (int a = 0; a < h.dim; ++a) p.hd *= hh;
+    const InvParams p = make_inv_params(h.dim, h.L / (double)h.N, h.kappa1, h.kappa2, h.mu, h.gamma);
     Grid g{h.dim, h.N, h.M};
     g.split = true;
-    const int nb = invariants_blocks(h.M);
+    const int nb = invariants_blocks(h.dim, h.N);
     const char* base = b->arena + h.off;
     int n = (h.precision == 64)
                 ? launch_invariants<double>(g, reinterpret_cast<const double2*>(base),

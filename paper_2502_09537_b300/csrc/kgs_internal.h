@@ -122,11 +122,25 @@ int launch_split_convert(const Grid& g, bool to_split, const vec2_t<T>* pq_in, c
 
 // Invariants (kgs_reduce.cu): E_h, its absolute-term scale, and the mass.
 struct InvParams {
-    double kappa1, kappa2, mu, gamma;
-    double inv_h2;  // 1 / h^2
-    double hd;      // h^dim
+    double k1, k2;          // kappa1 / (2 h^2), kappa2 / (2 h^2)
+    double abs_k1, abs_k2;  // their absolute values
+    double mu2, gamma;      // mu^2, gamma
+    double hd;              // h^dim
 };
-int invariants_blocks(int64_t M);
+inline InvParams make_inv_params(int dim, double h, double kappa1, double kappa2, double mu, double gamma)
+{
+    InvParams p;
+    p.k1 = kappa1 / (2.0 * h * h);
+    p.k2 = kappa2 / (2.0 * h * h);
+    p.abs_k1 = p.k1 < 0 ? -p.k1 : p.k1;
+    p.abs_k2 = p.k2 < 0 ? -p.k2 : p.k2;
+    p.mu2 = mu * mu;
+    p.gamma = gamma;
+    p.hd = 1.0;
+    for (int a = 0; a < dim; ++a) p.hd *= h;
+    return p;
+}
+int invariants_blocks(int dim, int64_t N);
 template <typename T>
 int launch_invariants(const Grid& g, const vec2_t<T>* pq, const vec2_t<T>* uv,
                       const InvParams& p, double* partials, int nblocks, double* out3,

@@ -84,14 +84,12 @@ __global__ void __launch_bounds__(kThreads) noalloc_partials_kernel(
             gp += dp * dp + dq * dq;
             gu += du * du;
         }
-        const double t1 = 0.5 * p.kappa1 * gp * p.inv_h2;
-        const double t2 = 0.5 * p.kappa2 * gu * p.inv_h2;
-        const double t3 = 0.5 * v0 * v0;
-        const double t4 = 0.5 * p.mu * p.mu * u0 * u0;
-        const double rho = p0 * p0 + q0 * q0;
-        const double t5 = p.gamma * rho * u0;
-        acc_add(e, t1 + t2 + t3 + t4 - t5);
-        acc_add(sc, fabs(t1) + fabs(t2) + t3 + t4 + fabs(t5));
+        // kappa1/2 |grad psi|^2 + kappa2/2 |grad u|^2 + (v^2 + mu^2 u^2)/2 - gamma |psi|^2 u
+        const double rho = fma(p0, p0, q0 * q0);
+        const double vu = fma(v0, v0, (p.mu2 * u0) * u0);
+        const double t5 = (p.gamma * rho) * u0;
+        acc_add(e, fma(p.k1, gp, fma(p.k2, gu, fma(0.5, vu, -t5))));
+        acc_add(sc, fma(p.abs_k1, gp, fma(p.abs_k2, gu, fma(0.5, vu, fabs(t5)))));
         acc_add(ms, rho);
     }
     double v[3] = {e.s + e.c, sc.s + sc.c, ms.s + ms.c};
@@ -183,15 +181,7 @@ extern "C" int kgs_invariants_noalloc(int dim, int64_t N, double L, double kappa
     double* partials = nullptr;
     int st = scratch_address(&partials);
     if (st != KGS_OK) return st;
-    kgs::InvParams p;
-    const double h = L / (double)N;
-    p.kappa1 = kappa1;
-    p.kappa2 = kappa2;
-    p.mu = mu;
-    p.gamma = gamma;
-    p.inv_h2 = 1.0 / (h * h);
-    p.hd = 1.0;
-    for (int a = 0; a < dim; ++a) p.hd *= h;
+    const kgs::InvParams p = kgs::make_inv_params(dim, L / (double)N, kappa1, kappa2, mu, gamma);
     const int nctas = (int)((M + kPointsPerCta - 1) / kPointsPerCta);
     cudaStream_t s = (cudaStream_t)stream;
     if (dim == 1)

@@ -216,6 +216,28 @@ def test_invariants_match_oracle(orc, dim, N):
     assert abs(M - Mo) <= 1e-13 * Mo
 
 
+@pytest.mark.parametrize("dim,N", [(1, 64), (2, 24), (2, 2048), (3, 10), (3, 18)])
+def test_invariants_of_fp32_state_match_oracle(orc, dim, N):
+    """The FP32 state is widened to float64 exactly before differencing: the
+    invariants equal the oracle's on the float-rounded state, including signed
+    zeros and subnormal values (the widening's special cases)."""
+    prob = Problem(dim, N, 7.0, 1.3, -0.7, 0.9, 1.1, 0.01)
+    st = [a.astype(np.float32) for a in random_state(prob, 60 + dim, 0.8)]
+    flat = [a.reshape(-1) for a in st]
+    flat[3][::7] = 0.0
+    flat[3][1::11] = -0.0
+    flat[0][2::13] = np.float32(1e-40)
+    flat[1][3::17] = np.float32(-3e-39)
+    st64 = [a.astype(np.float64) for a in st]
+    with Solver.from_problem(prob, KGS_FP32) as s:
+        s.set_state(*copy_state(st64))
+        E, S, M = s.invariants()
+    Eo, So, Mo = orc.invariants(prob, *st64)
+    assert abs(E - Eo) <= 1e-13 * So
+    assert abs(S - So) <= 1e-13 * So
+    assert abs(M - Mo) <= 1e-13 * Mo
+
+
 def test_energy_conserved_on_gpu_over_1e4_steps():
     prob = Problem(2, 32, 2 * math.pi, 1.0, 1.0, 1.0, 1.0, 0.05)
     st = random_state(prob, 12, 0.6)
