@@ -442,8 +442,10 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent, "
-                         "5 slab-pipelined passes")
-    ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab kernel)")
+                         "5 slab-pipelined passes, 6 wave (a step's two passes in one launch)")
+    ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab and wave kernels)")
+    ap.add_argument("--wave-lag", type=int, default=0, help="KGS_OPT_WAVE_LAG (wave kernel)")
+    ap.add_argument("--wave-chunk", type=int, default=0, help="KGS_OPT_WAVE_CHUNK (wave kernel)")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
     ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block"],
                     help="update order: the checkerboard (Algorithm 3), the lexicographic "
@@ -503,6 +505,12 @@ def main():
     if args.slab_planes:
         from paper_2502_09537_b300.solver import KGS_OPT_SLAB_PLANES
         s.set_option(KGS_OPT_SLAB_PLANES, args.slab_planes)
+    if args.wave_lag:
+        from paper_2502_09537_b300.solver import KGS_OPT_WAVE_LAG
+        s.set_option(KGS_OPT_WAVE_LAG, args.wave_lag)
+    if args.wave_chunk:
+        from paper_2502_09537_b300.solver import KGS_OPT_WAVE_CHUNK
+        s.set_option(KGS_OPT_WAVE_CHUNK, args.wave_chunk)
     if args.order_mode:
         from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
         s.set_option(KGS_OPT_ORDER_MODE, args.order_mode)
@@ -602,7 +610,8 @@ def main():
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
                    "threads": args.threads or 256, "kernel": args.kernel, "order": args.order,
                    "order_mode": args.order_mode,
-                   "slab_planes": args.slab_planes,
+                   "slab_planes": args.slab_planes, "wave_lag": args.wave_lag,
+                   "wave_chunk": args.wave_chunk,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",

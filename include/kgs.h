@@ -53,8 +53,9 @@ extern "C" {
 #define KGS_ERR_CUDA     -4  /* a CUDA call failed (also: no usable device) */
 #define KGS_ERR_STATE    -5  /* no state set yet */
 #define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out (a grid barrier of the persistent
-                               order launch did not complete within 2 s); the handle's state is
-                               lost and every later call on the handle returns this status */
+                               order launch or a dependency wait of the wave kernel did not
+                               complete within 2 s); the handle's state is lost and every later
+                               call on the handle returns this status */
 #define KGS_ERR_RANGE    -7  /* size beyond what the call supports */
 
 /* memory kind of caller buffers */
@@ -70,7 +71,12 @@ extern "C" {
                                3 temporally blocked tiles (dim 2, 3; allocates a second state
                                buffer of the same size on first use), 4 persistent grid-stride
                                colour passes, 5 colour passes pipelined in axis-0 slabs through
-                               L2 (dim 2, 3; see KGS_OPT_SLAB_PLANES) */
+                               L2 (dim 2, 3; see KGS_OPT_SLAB_PLANES), 6 wave kernel: a step's
+                               two colour passes in one cooperative launch whose CTAs take
+                               slab chunks in a dependency-safe order (dim 2, 3, N >= 64;
+                               KGS_OPT_SLAB_PLANES sets the slab, 0 = about 4 MB of state;
+                               grids it does not fit run the plain passes).  All give
+                               bitwise the same state. */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
 #define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
 #define KGS_OPT_PPT      4  /* points of one colour per thread in those kernels: 1 only (2 was
@@ -91,11 +97,21 @@ extern "C" {
                                    first use; each kgs_step call converts into it and back).  All
                                    compute bitwise the same state. */
 #define KGS_OPT_TEST_BARRIER_STALL 12  /* test hook: n > 0 makes every grid barrier of the
-                                   persistent order launch wait for n CTAs that do not exist, so
-                                   it times out (after 2 s) and kgs_step returns KGS_ERR_TIMEOUT;
+                                   persistent order launch wait for n CTAs that do not exist, and
+                                   every dependency wait of the wave kernel for n chunks that do
+                                   not exist, so they time out (after 2 s) and the handle reports
+                                   KGS_ERR_TIMEOUT (kgs_step for the order launch, which waits for
+                                   the device; the next synchronising call for the wave kernel);
                                    0 (default) off.  For testing the timeout path only. */
-#define KGS_OPT_SLAB_PLANES 10  /* slab kernel: axis-0 planes per slab, 1 .. N; 0 (default) picks
-                                   about a quarter of the L2 cache's bytes per slab.  A step's
+#define KGS_OPT_WAVE_LAG    13  /* wave kernel: slabs by which the red pass trails the black pass
+                                   in the ticket order, 1 .. 64; 0 (default) = enough for the
+                                   chunks in flight (2 + CTAs / (2 chunks per slab)) */
+#define KGS_OPT_WAVE_CHUNK  14  /* wave kernel: points of a colour per chunk (rounded down to
+                                   whole rows, at least one), 1 .. 2^24; 0 (default) = 2048 */
+#define KGS_OPT_SLAB_PLANES 10  /* slab and wave kernels: axis-0 planes per slab, 1 .. N (the
+                                   wave kernel takes the largest divisor of N not above it);
+                                   0 (default) picks about a quarter of the L2 cache's bytes per
+                                   slab for the slab kernel.  A step's
                                    black pass runs slab by slab and each slab's red pass follows
                                    the next slab's black pass, so the two passes reuse the state
                                    in L2 instead of reading it from HBM twice; every point sees

@@ -80,6 +80,15 @@ struct kgs_solver {
     int opt_order_mode = 0;            // 0 auto, 1 levels on the split layout, 2 persistent, 3 levels on natural order
     int opt_stall = 0;                 // test hook: phantom CTAs every barrier waits for
     bool timed_out = false;            // a bounded device wait ran out: the state is lost
+    // wave kernel (KGS_OPT_KERNEL 6): plan (0 not made, 1 usable, -1 not
+    // applicable: plain passes), its counters and the timeout word (pinned,
+    // mapped, so the host reads it without a copy)
+    WaveParams wplan{};
+    int wplan_state = 0;
+    unsigned* wsync = nullptr;
+    int* werr = nullptr;
+    int opt_wave_lag = 0;
+    int64_t opt_wave_chunk = 0;
 };
 
 namespace {
@@ -109,6 +118,7 @@ int cuda_fail(kgs_solver* h, cudaError_t e, const char* what)
 int check_handle(kgs_solver* h)
 {
     if (!h) return fail(KGS_ERR_ARG, "NULL handle");
+    if (h->werr && *(volatile int*)h->werr) h->timed_out = true;
     if (h->timed_out)
         return fail(KGS_ERR_TIMEOUT, "handle is in error state after a device wait timed out");
     if (h->sticky)
@@ -148,7 +158,7 @@ Grid grid_of(const kgs_solver* h)
     return g;
 }
 
-enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5 };
+enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5, K_WAVE = 6 };
 
 // Default tile shape per dimension and precision (measured on B300; the batch
 // autotuner can override it per handle).
@@ -168,7 +178,7 @@ TileParams default_tile(int dim, int precision)
 int kernel_choice(const kgs_solver* h)
 {
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
-    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_SLAB) return h->opt_kernel;
+    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_WAVE) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
     // Measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass beats the
     // temporally blocked tiles in both precisions (FP32: 8.6e10 vs 6.2e10 /
@@ -222,6 +232,47 @@ int64_t slab_planes(const kgs_solver* h)
     return p < h->N ? p : h->N;
 }
 
+// The wave kernel's plan and buffers; returns 1 if it applies to the grid, 0
+// if not (the plain passes run instead), or a negative status.
+int ensure_wave(kgs_solver* h)
+{
+    if (h->wplan_state) return h->wplan_state > 0;
+    WaveParams wp;
+    const int elem = h->precision == 64 ? 8 : 4;
+    if (wave_plan(h->dim, h->N, elem, h->opt_slab, h->opt_wave_lag, h->opt_wave_chunk, wave_ctas(h->dim, elem, h->M),
+                  wp)) {
+        h->wplan_state = -1;
+        return 0;
+    }
+    cudaFree(h->wsync);
+    h->wsync = nullptr;
+    cudaError_t e = cudaMalloc(&h->wsync, (size_t)(2 + 2 * wp.ns) * sizeof(unsigned));
+    if (e == cudaSuccess && !h->werr) {
+        e = cudaHostAlloc(&h->werr, sizeof(int), cudaHostAllocMapped);
+        if (e == cudaSuccess) *(volatile int*)h->werr = 0;
+        else h->werr = nullptr;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA, "wave kernel buffers: %s",
+                    cudaGetErrorString(e));
+    }
+    h->wplan = wp;
+    h->wplan_state = 1;
+    return 1;
+}
+
+// A wave launch whose wait timed out leaves the state undefined; read after
+// a synchronisation of the handle's work.
+int wave_status(kgs_solver* h)
+{
+    if (h->werr && *(volatile int*)h->werr) {
+        h->timed_out = true;
+        return fail(KGS_ERR_TIMEOUT, "a dependency wait of the wave kernel timed out");
+    }
+    return KGS_OK;
+}
+
 // One (BLACK_FUSED, red) pair of colour passes, red = RED_FUSED or RED_ADJ.
 // With the slab kernel the black pass runs slab by slab along axis 0 and the
 // red pass of slab s - 1 follows the black pass of slab s: the red pass of a
@@ -237,6 +288,17 @@ int pass_pair(kgs_solver* h, int red, cudaStream_t s)
     vec2_t<T>* pq = (vec2_t<T>*)h->pqb[h->cur];
     vec2_t<T>* uv = (vec2_t<T>*)h->uvb[h->cur];
     Grid g = grid_of(h);
+    if (kernel_choice(h) == K_WAVE) {
+        const int w = ensure_wave(h);
+        if (w < 0) return -1;
+        if (w > 0) {
+            WaveParams wp = h->wplan;
+            wp.stall = h->opt_stall;
+            if (launch_wave<T>(g, red, pq, uv, *c, wp, h->wsync, h->werr, s) < 0) return -1;
+            h->launches += 1;
+            return 0;
+        }
+    }
     if (kernel_choice(h) != K_SLAB || h->dim < 2) {
         if (launch_pass<T>(g, BLACK_FUSED, pq, uv, *c, s) < 0 || launch_pass<T>(g, red, pq, uv, *c, s) < 0)
             return -1;
@@ -268,6 +330,8 @@ int ensure_graph(kgs_solver* h)
 {
     if (h->graph && h->graph_buf == h->cur) return 0;
     drop_graph(h);
+    // allocations are not allowed while a stream is being captured
+    if (kernel_choice(h) == K_WAVE && ensure_wave(h) < 0) return KGS_ERR_CUDA;
     if (!h->capture_stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
@@ -537,6 +601,10 @@ void free_all(kgs_solver* h)
     cudaFree(h->olist);
     cudaFree(h->olevels_dev);
     cudaFree(h->obar);
+    cudaFree(h->wsync);
+    if (h->werr) cudaFreeHost(h->werr);
+    h->wsync = nullptr;
+    h->werr = nullptr;
     h->olist = nullptr;
     h->olevels_dev = nullptr;
     h->obar = nullptr;
@@ -702,6 +770,7 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int 
     if (where == KGS_HOST) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        return wave_status(h);
     }
     return KGS_OK;
 }
@@ -813,6 +882,7 @@ int kgs_invariants(kgs_handle h, double* out3, void* stream)
     cudaError_t e = cudaMemcpyAsync(h->out_host, h->out_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "invariants readback");
+    if ((st = wave_status(h))) return st;
     for (int k = 0; k < 3; ++k) out3[k] = h->out_host[k];
     return KGS_OK;
 }
@@ -852,8 +922,9 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     if (st) return st;
     switch (option) {
     case KGS_OPT_KERNEL:
-        if (value < 0 || value > 5) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 5");
+        if (value < 0 || value > 6) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 6");
         if (value == 5 && h->dim < 2) return fail(KGS_ERR_ARG, "the slab kernel needs dim 2 or 3");
+        if (value == 6 && h->dim < 2) return fail(KGS_ERR_ARG, "the wave kernel needs dim 2 or 3");
         if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))
             return fail(KGS_ERR_RANGE, "grid too large for the shared-memory resident kernel");
         if (value == 3 && h->dim < 2)
@@ -904,6 +975,19 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     case KGS_OPT_SLAB_PLANES:
         if (value < 0 || value > h->N) return fail(KGS_ERR_ARG, "KGS_OPT_SLAB_PLANES takes 0 to N");
         h->opt_slab = value;
+        h->wplan_state = 0;
+        drop_graph(h);
+        return KGS_OK;
+    case KGS_OPT_WAVE_CHUNK:
+        if (value < 0 || value > ((int64_t)1 << 24)) return fail(KGS_ERR_ARG, "KGS_OPT_WAVE_CHUNK takes 0 to 2^24");
+        h->opt_wave_chunk = value;
+        h->wplan_state = 0;
+        drop_graph(h);
+        return KGS_OK;
+    case KGS_OPT_WAVE_LAG:
+        if (value < 0 || value > 64) return fail(KGS_ERR_ARG, "KGS_OPT_WAVE_LAG takes 0 to 64");
+        h->opt_wave_lag = (int)value;
+        h->wplan_state = 0;
         drop_graph(h);
         return KGS_OK;
     case KGS_OPT_THREADS:

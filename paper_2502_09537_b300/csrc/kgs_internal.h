@@ -56,6 +56,26 @@ template <typename T>
 int launch_smem_run(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
                     int64_t nsteps, cudaStream_t stream);
 
+// One (BLACK_FUSED, red_mode) pair of colour passes in one cooperative launch
+// (kgs_sweep.cu: wave_kernel): slabs of S axis-0 planes, chunks of `rows`
+// rows, taken in a dependency-safe ticket order; red slab j waits for black
+// slabs j-1, j, j+1.  wave_ctas: the launch's CTAs (all co-resident).
+// wave_plan fills the parameters for a grid and that many CTAs (0), or
+// returns -1 where the wave schedule does not apply (1D, N < 64, too few
+// slabs for the lag).  sync: 2 + 2 ns unsigned words on the device (zeroed by the
+// launcher on the stream); err: a word the kernel sets to 1 if a wait timed
+// out (2 s; stall > 0 makes every wait need that many extra chunks, which
+// tests the timeout).  launch_wave returns 1, or -1 if the launch failed.
+struct WaveParams {
+    int S = 0, ns = 0, rows = 0, chunks = 0, lag = 2, stall = 0;
+};
+int wave_ctas(int dim, int elem_bytes, int64_t M);
+int wave_plan(int dim, int64_t N, int elem_bytes, int64_t want_S, int want_lag, int64_t want_chunk, int ctas,
+              WaveParams& wp);
+template <typename T>
+int launch_wave(const Grid& g, int red_mode, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                const WaveParams& wp, unsigned* sync, int* err, cudaStream_t s);
+
 // Temporally blocked colour passes (kgs_tile.cu): passes g0 .. g0+P-1 of an
 // nsteps-step run in one launch, reading (pq, uv) and writing (pq_out, uv_out).
 struct TileParams {

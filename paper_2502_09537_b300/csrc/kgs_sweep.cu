@@ -108,30 +108,19 @@ __device__ __forceinline__ void colour_update(vec2_t<T>* pq, vec2_t<T>* uv, int6
     u[iv] = V;
 }
 
-// One launch per colour pass.  The launch grid carries the row coordinates
-// (blockIdx.y = axis D-2, blockIdx.z = axis 0 for D = 3), so a thread finds its
-// point without divisions; blockIdx.x * blockDim.x + threadIdx.x runs over the
-// N/2 points of the pass's colour in the row.  32-bit indices when N^d < 2^31.
-template <typename T, int D, int MODE, typename I>
-__global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c,
-                                                   int parity, int plane0)
+// Update the point k of row (i0, i1) (axis-0 and axis-1 coordinates; i1 = 0
+// in 2D, both 0 in 1D) of the colour with 0-based index-sum parity `parity`,
+// on the colour-split layout.  N_I = N in the index type I.  NC: read the
+// other colour through the non-coherent (read-only) path, valid when no
+// other CTA writes it during the launch; otherwise plain (coherent) loads.
+template <typename T, int D, int MODE, typename I, bool NC>
+__device__ __forceinline__ void pass_point(vec2_t<T>* pq, vec2_t<T>* uv, int N, const Coef<T>& c,
+                                           int i0, int i1, int k)
 {
-    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (2 * kk >= N) return;
     const I n = N;
-    int i0 = 0, i1 = 0, rp = 0;
     I row = 0;
-    if (D == 2) {
-        i0 = plane0 + (int)blockIdx.y;
-        rp = i0 & 1;
-        row = i0;
-    } else if (D == 3) {
-        i0 = plane0 + (int)blockIdx.z;
-        i1 = blockIdx.y;
-        rp = (i0 + i1) & 1;
-        row = (I)i0 * n + i1;
-    }
-    const int k = 2 * kk + ((parity - rp) & 1);
+    if (D == 2) row = i0;
+    else if (D == 3) row = (I)i0 * n + i1;
     const I i = row * n + k;
     I nb[2 * D];
     const I km = (k == 0) ? i + (n - 1) : i - 1;
@@ -154,6 +143,7 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
         nb[5] = kp;
     }
     // colour-split layout: this colour's half from pq + own, the other's from pq + oth
+    const int parity = (i0 + i1 + k) & 1;
     const I half = (D == 1 ? n : (D == 2 ? n * n : n * n * n)) >> 1;
     const I own = (parity ? half : 0) + (i >> 1);
     const I oth = parity ? 0 : half;
@@ -161,11 +151,11 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
-        const I k = oth + (nb[m] >> 1);
-        const vec2_t<T> b = __ldg(&pq[k]);
+        const I j = oth + (nb[m] >> 1);
+        const vec2_t<T> b = NC ? __ldg(&pq[j]) : pq[j];
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = __ldg(&u[k]);
+        w[m] = NC ? __ldg(&u[j]) : u[j];
     }
     vec2_t<T> a = pq[own];
     T U = u[own], V = u[2 * half + own];
@@ -173,6 +163,29 @@ __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv,
     pq[own] = a;
     u[own] = U;
     u[2 * half + own] = V;
+}
+
+// One launch per colour pass.  The launch grid carries the row coordinates
+// (blockIdx.y = axis D-2, blockIdx.z = axis 0 for D = 3), so a thread finds its
+// point without divisions; blockIdx.x * blockDim.x + threadIdx.x runs over the
+// N/2 points of the pass's colour in the row.  32-bit indices when N^d < 2^31.
+template <typename T, int D, int MODE, typename I>
+__global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c,
+                                                   int parity, int plane0)
+{
+    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * kk >= N) return;
+    int i0 = 0, i1 = 0, rp = 0;
+    if (D == 2) {
+        i0 = plane0 + (int)blockIdx.y;
+        rp = i0 & 1;
+    } else if (D == 3) {
+        i0 = plane0 + (int)blockIdx.z;
+        i1 = blockIdx.y;
+        rp = (i0 + i1) & 1;
+    }
+    const int k = 2 * kk + ((parity - rp) & 1);
+    pass_point<T, D, MODE, I, true>(pq, uv, N, c, i0, i1, k);
 }
 
 // Persistent variant: a grid sized so that every thread gets nearly the same
@@ -187,6 +200,232 @@ __global__ void __launch_bounds__(256) pass_persistent_kernel(vec2_t<T>* pq, vec
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride)
         colour_update<T, D, MODE, true>(pq, uv, t, N, half, parity, c);
+}
+
+// ------------------------------------------------------------------ wave --
+// One (BLACK_FUSED, REDMODE) pair of colour passes in one launch, so that a
+// step reads and writes the state about once instead of once per pass.  The
+// grid is cut along axis 0 into ns slabs of S planes; an item is one colour
+// of one slab, cut into `chunks` chunks of `rows` rows (lines along the last
+// axis).  Persistent CTAs take chunks in ticket order (one atomic counter):
+//   B(0) .. B(lag), then B(k), R(k - lag) for k = lag+1 .. ns-1,
+//   then R(ns-lag) .. R(ns-1), R(0),
+// B = black, R = red.  A red slab needs the black slabs on both sides
+// updated, and a black slab needs the red slabs on both sides not yet
+// updated; so R(j) waits until B(j-1), B(j), B(j+1) (periodic) are complete,
+// and comes after B(j+1) in ticket order (R(0), whose lower neighbour is
+// B(ns-1), goes last).  Black chunks never wait.  A CTA takes its tickets in
+// increasing order and a chunk waits only for chunks with earlier tickets,
+// held by running CTAs, so the schedule cannot deadlock; the launch is
+// cooperative all the same (all CTAs resident), and a wait longer than
+// kWaveWaitNs sets the error words, after which every CTA leaves.  Black
+// chunks read red values that no CTA writes before they finish, so the only
+// cross-CTA reads are the red chunks' reads of black values, ordered by a
+// release (CTA barrier, then thread 0's counter increment) and an acquire
+// (thread 0's counter read, then a CTA barrier); the loads are plain,
+// coherent ones (not the read-only path).  The pointwise code is pass_point,
+// so the result is bitwise that of the two passes.  (Measured on B300 with
+// FP32 state, 3D 256^3: 26% fewer DRAM bytes than the two passes, but at 37%
+// of DRAM peak against their 67% -- latency-bound on the per-chunk barriers
+// and the pipeline's fill and drain -- so it stays opt-in.)
+constexpr uint64_t kWaveWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t wave_clock_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void add_release(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Item q of the ticket order: colour (1 = red) and slab.
+__device__ __forceinline__ void wave_item(int q, int ns, int lag, int& red, int& slab)
+{
+    const int a = lag + 1, mid = 2 * (ns - 1 - lag);
+    if (q < a) {
+        red = 0;
+        slab = q;
+    } else if (q < a + mid) {
+        const int r = q - a, k = a + (r >> 1);
+        red = r & 1;
+        slab = red ? k - lag : k;
+    } else {
+        const int r = q - a - mid;
+        red = 1;
+        slab = r < lag ? ns - lag + r : 0;
+    }
+}
+
+template <typename T, int D, int MODE, typename I>
+__device__ __forceinline__ void wave_chunk(vec2_t<T>* pq, vec2_t<T>* uv, int N, const Coef<T>& c,
+                                           const WaveParams& wp, int slab, int chunk)
+{
+    const int parity = MODE == BLACK_FUSED ? (red_parity(D) ^ 1) : red_parity(D);
+    const int rows_per_plane = D == 3 ? N : 1;
+    const int row0 = slab * wp.S * rows_per_plane + chunk * wp.rows;
+    const int hN = N >> 1;
+    // the chunk's rows x N/2 points of the colour, spread over all threads
+    for (int e = threadIdx.x; e < wp.rows * hN; e += blockDim.x) {
+        const int r = e / hN, kk = e - r * hN;
+        const int row = row0 + r;
+        const int i0 = D == 3 ? row / N : row;
+        const int i1 = D == 3 ? row - i0 * N : 0;
+        const int rp = (i0 + i1) & 1;
+        pass_point<T, D, MODE, I, false>(pq, uv, N, c, i0, i1, 2 * kk + ((parity - rp) & 1));
+    }
+}
+
+template <typename T, int D, int REDMODE, typename I>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 3)
+    wave_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c, WaveParams wp, unsigned* sync, int* err)
+{
+    __shared__ int s_ticket, s_go;
+    const int total = 2 * wp.ns * wp.chunks;
+    unsigned* derr = sync + 1;  // device copy of the error word
+    unsigned* done = sync + 2;  // black slab k at k, red slab k at ns + k
+    // thread 0 fetches the next ticket while the CTA works on the current one
+    // (the CTA still takes its tickets in increasing order)
+    int next = threadIdx.x == 0 ? (int)atomicAdd(&sync[0], 1u) : 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = next;
+            int go = t < total;
+            if (go) {
+                int red, slab;
+                wave_item(t / wp.chunks, wp.ns, wp.lag, red, slab);
+                if (red) {
+                    const unsigned need = (unsigned)(wp.chunks + wp.stall);
+                    const int nb[3] = {slab == 0 ? wp.ns - 1 : slab - 1, slab, slab == wp.ns - 1 ? 0 : slab + 1};
+                    const uint64_t t0 = wave_clock_ns();
+                    for (int k = 0; k < 3 && go; ++k) {
+                        while (load_acquire(&done[nb[k]]) < need) {
+                            if (*(volatile unsigned*)derr || wave_clock_ns() - t0 > kWaveWaitNs) {
+                                *(volatile unsigned*)derr = 1u;
+                                *(volatile int*)err = 1;
+                                go = 0;
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
+                }
+            }
+            if (go) next = (int)atomicAdd(&sync[0], 1u);
+            s_ticket = t;
+            s_go = go;
+        }
+        __syncthreads();  // also carries thread 0's acquire to the CTA
+        const int t = s_ticket;
+        if (!s_go) break;
+        int red, slab;
+        wave_item(t / wp.chunks, wp.ns, wp.lag, red, slab);
+        const int chunk = t % wp.chunks;
+        if (red) wave_chunk<T, D, REDMODE, I>(pq, uv, N, c, wp, slab, chunk);
+        else wave_chunk<T, D, BLACK_FUSED, I>(pq, uv, N, c, wp, slab, chunk);
+        __syncthreads();  // the CTA's stores precede thread 0's release
+        if (threadIdx.x == 0) add_release(&done[(red ? wp.ns : 0) + slab], 1u);
+    }
+}
+
+// Co-resident CTAs of the wave kernel for a grid (the cooperative launch's size).
+template <typename T, int D>
+static int wave_ctas_t(int64_t M)
+{
+    auto kern = M < ((int64_t)1 << 31) ? wave_kernel<T, D, RED_FUSED, int32_t> : wave_kernel<T, D, RED_FUSED, int64_t>;
+    int dev = 0, sms = 148, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0) != cudaSuccess || per < 1) return -1;
+    return sms * per;
+}
+
+int wave_ctas(int dim, int elem_bytes, int64_t M)
+{
+    if (dim == 2) return elem_bytes == 8 ? wave_ctas_t<double, 2>(M) : wave_ctas_t<float, 2>(M);
+    if (dim == 3) return elem_bytes == 8 ? wave_ctas_t<double, 3>(M) : wave_ctas_t<float, 3>(M);
+    return -1;
+}
+
+int wave_plan(int dim, int64_t N, int elem_bytes, int64_t want_S, int want_lag, int64_t want_chunk, int ctas,
+              WaveParams& wp)
+{
+    if (dim < 2 || N < 64 || N > 65536 || ctas < 1) return -1;
+    const int rows_per_plane = dim == 3 ? (int)N : 1;
+    const int64_t plane_bytes = (dim == 3 ? N * N : N) * 4 * (int64_t)elem_bytes;
+    // slab: about 4 MB of state unless given, and at most N/8 planes (so that
+    // a small grid still gets a pipeline of slabs); S divides N
+    int64_t S = want_S > 0 ? want_S
+                           : std::max<int64_t>(1, std::min<int64_t>(((int64_t)4 << 20) / plane_bytes, N / 8));
+    if (S > N) S = N;
+    while (N % S) --S;
+    const int64_t ns = N / S;
+    // chunk: about 2048 points of a colour unless given (whole rows)
+    const int64_t half_row = N / 2;
+    int64_t rows = std::max<int64_t>(1, (want_chunk > 0 ? want_chunk : 2048) / half_row);
+    const int64_t slab_rows = S * rows_per_plane;
+    if (rows > slab_rows) rows = slab_rows;
+    while (slab_rows % rows) --rows;
+    const int64_t chunks = slab_rows / rows;
+    if (2 * ns * chunks >= ((int64_t)1 << 31)) return -1;
+    // lag: the red slabs trail far enough that the black slabs they wait for
+    // have left the window of chunks in flight (one per CTA), unless given
+    int64_t lag = want_lag > 0 ? want_lag : 2 + (ctas + 2 * chunks - 1) / (2 * chunks);
+    if (want_lag <= 0 && lag > ns - 2) lag = ns - 2;
+    if (lag < 1 || ns < lag + 2) return -1;
+    wp.S = (int)S;
+    wp.ns = (int)ns;
+    wp.rows = (int)rows;
+    wp.chunks = (int)chunks;
+    wp.lag = lag;
+    wp.stall = 0;
+    return 0;
+}
+
+template <typename T, int D, int REDMODE>
+static int launch_wave_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c, const WaveParams& wp,
+                         unsigned* sync, int* err, cudaStream_t s)
+{
+    auto kern = g.M < ((int64_t)1 << 31) ? wave_kernel<T, D, REDMODE, int32_t> : wave_kernel<T, D, REDMODE, int64_t>;
+    int dev = 0, sms = 148, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0) != cudaSuccess || per < 1) return -1;
+    const int64_t total = 2 * (int64_t)wp.ns * wp.chunks;
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sms * per, total);
+    // every CTA may fetch one ticket past the end
+    if (total + grid >= ((int64_t)1 << 31)) return -1;
+    if (cudaMemsetAsync(sync, 0, (size_t)(2 + 2 * wp.ns) * sizeof(unsigned), s) != cudaSuccess) return -1;
+    int n = (int)g.N;
+    Coef<T> cc = c;
+    WaveParams w = wp;
+    void* args[] = {&pq, &uv, &n, &cc, &w, &sync, &err};
+    if (cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, 0, s) != cudaSuccess) return -1;
+    return 1;
+}
+
+template <typename T>
+int launch_wave(const Grid& g, int red_mode, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& c,
+                const WaveParams& wp, unsigned* sync, int* err, cudaStream_t s)
+{
+    const bool adj = red_mode == RED_ADJ;
+    if (g.dim == 2)
+        return adj ? launch_wave_t<T, 2, RED_ADJ>(g, pq, uv, c, wp, sync, err, s)
+                   : launch_wave_t<T, 2, RED_FUSED>(g, pq, uv, c, wp, sync, err, s);
+    if (g.dim == 3)
+        return adj ? launch_wave_t<T, 3, RED_ADJ>(g, pq, uv, c, wp, sync, err, s)
+                   : launch_wave_t<T, 3, RED_FUSED>(g, pq, uv, c, wp, sync, err, s);
+    return -1;
 }
 
 template <typename T, int D, int MODE>
@@ -346,6 +585,10 @@ int launch_smem_run(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coef<T>& 
 
 template int launch_pass<double>(const Grid&, int, double2*, double2*, const Coef<double>&, cudaStream_t);
 template int launch_pass<float>(const Grid&, int, float2*, float2*, const Coef<float>&, cudaStream_t);
+template int launch_wave<double>(const Grid&, int, double2*, double2*, const Coef<double>&, const WaveParams&,
+                                 unsigned*, int*, cudaStream_t);
+template int launch_wave<float>(const Grid&, int, float2*, float2*, const Coef<float>&, const WaveParams&,
+                                unsigned*, int*, cudaStream_t);
 template int launch_smem_run<double>(const Grid&, double2*, double2*, const Coef<double>&, int64_t, cudaStream_t);
 template int launch_smem_run<float>(const Grid&, float2*, float2*, const Coef<float>&, int64_t, cudaStream_t);
 

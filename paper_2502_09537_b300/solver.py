@@ -35,6 +35,8 @@ KGS_OPT_TILE_THREADS = 9
 KGS_OPT_SLAB_PLANES = 10
 KGS_OPT_ORDER_MODE = 11
 KGS_OPT_TEST_BARRIER_STALL = 12
+KGS_OPT_WAVE_LAG = 13
+KGS_OPT_WAVE_CHUNK = 14
 KGS_ERR_TIMEOUT = -6
 
 # Every function the header declares, with its ctypes signature.

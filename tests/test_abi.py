@@ -102,3 +102,16 @@ def test_valid_create_without_gpu_fails_loudly(lib):
     assert lib.kgs_last_status() == -4
     with pytest.raises(solver.KGSError):
         solver.Solver(2, 16, 1.0, 1, 1, 1, 1, 0.1)
+
+
+def test_binding_constants_match_the_header():
+    """Every KGS_* constant the Python binding defines has the value
+    include/kgs.h gives it."""
+    text = open(HEADERS[0]).read()
+    defines = {m.group(1): int(m.group(2))
+               for m in re.finditer(r"^#define\s+(KGS_\w+)\s+(-?\d+)\b", text, flags=re.M)}
+    names = [n for n in dir(solver) if n.startswith("KGS_")]
+    assert len(names) > 10
+    for n in names:
+        assert n in defines, f"{n} not in kgs.h"
+        assert getattr(solver, n) == defines[n], n

@@ -139,6 +139,59 @@ def test_slab_pipelined_passes_are_bitwise_the_full_passes(dim, N, planes, preci
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+@pytest.mark.parametrize("dim,N,planes,lag", [(2, 64, 1, 0), (2, 64, 3, 1), (2, 130, 0, 0), (2, 130, 13, 3),
+                                              (2, 64, 64, 0), (3, 64, 1, 0), (3, 64, 4, 2), (3, 66, 0, 5)])
+def test_wave_kernel_is_bitwise_the_full_passes(dim, N, planes, lag, precision):
+    """The wave kernel (KGS_OPT_KERNEL = 6) runs a step's black and red passes
+    in one launch, slab chunks taken in a dependency-safe order with the red
+    slabs trailing by `lag`; the state is bitwise that of the two full passes
+    for any slab size and lag (one slab: the plain passes run instead)."""
+    from paper_2502_09537_b300.solver import KGS_OPT_SLAB_PLANES, KGS_OPT_WAVE_LAG
+    prob = Problem(dim, N, 9.0, 1.0, 0.9, 1.1, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 97 + planes, 0.5)
+    ref = run_gpu(prob, st, 45, precision=precision, kernel=1)
+    for graph in (1, 0):
+        with Solver.from_problem(prob, precision) as s:
+            s.set_option(KGS_OPT_KERNEL, 6)
+            s.set_option(KGS_OPT_SLAB_PLANES, planes)
+            s.set_option(KGS_OPT_WAVE_LAG, lag)
+            s.set_option(KGS_OPT_GRAPH, graph)
+            s.set_state(*copy_state(st))
+            s.step(40)     # the first call already replays a captured graph
+            s.step(5)
+            got = s.get_state()
+        for x, y in zip(ref, got):
+            assert np.array_equal(x, y)
+
+
+def test_wave_kernel_wait_timeout_is_reported_and_the_context_survives():
+    """A dependency wait that cannot complete (the test hook makes every red
+    chunk wait for chunks that do not exist) ends after its 2 s limit: the
+    kernel returns, the handle reports KGS_ERR_TIMEOUT at the next
+    synchronising call and from then on, and a new handle works."""
+    from paper_2502_09537_b300.solver import (KGS_ERR_TIMEOUT, KGS_OPT_SLAB_PLANES,
+                                              KGS_OPT_TEST_BARRIER_STALL, KGSError)
+    prob = Problem(3, 64, 9.0, 1.0, 0.9, 1.1, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 98, 0.5)
+    with Solver.from_problem(prob) as s:
+        s.set_option(KGS_OPT_KERNEL, 6)
+        s.set_option(KGS_OPT_SLAB_PLANES, 4)
+        s.set_option(KGS_OPT_TEST_BARRIER_STALL, 1)
+        s.set_state(*copy_state(st))
+        s.step(3)
+        with pytest.raises(KGSError) as ei:
+            s.invariants()
+        assert ei.value.status == KGS_ERR_TIMEOUT
+        with pytest.raises(KGSError) as ei:
+            s.step(1)
+        assert ei.value.status == KGS_ERR_TIMEOUT
+    ref = run_gpu(prob, st, 6, kernel=1)
+    got = run_gpu(prob, st, 6, kernel=6)
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("dim,N", [(2, 66), (3, 18), (1, 2050)])
 @pytest.mark.parametrize("threads,ppt", [(128, 1), (512, 1)])
 def test_launch_shapes_are_bitwise_equal(dim, N, threads, ppt):
