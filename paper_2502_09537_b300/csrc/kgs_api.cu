@@ -307,10 +307,18 @@ int pass_pair(kgs_solver* h, int red, cudaStream_t s)
     }
     const int64_t S = slab_planes(h), N = h->N;
     const int64_t ns = (N + S - 1) / S;
+    // the pair's first two launches (black slabs 0 and 1) wait for everything
+    // before them; the others are programmatic dependent launches (see
+    // pass_kernel): from the third on, every red launch waits for the black
+    // one just before it, and every black launch starts only after the red
+    // one before it has passed that wait, so each red slab finds its three
+    // black slabs complete
+    int index = 0;
     auto run = [&](int mode, int64_t p0, int64_t p1) -> int {
         if (p1 <= p0) return 0;
         g.plane0 = p0;
         g.planes = p1 - p0;
+        g.pdl = index++ >= 2;
         if (launch_pass<T>(g, mode, pq, uv, *c, s) < 0) return -1;
         h->launches += 1;
         return 0;

@@ -21,6 +21,7 @@ struct Grid {
     // means all N (one-launch-per-pass kernels only; 2D and 3D)
     int64_t plane0 = 0, planes = 0;
     bool split = false;  // state in the colour-split layout (below)
+    bool pdl = false;    // launch with programmatic dependent launch (slab schedule)
 };
 
 // Colour-split state layout (a handle's state): the points of even coordinate

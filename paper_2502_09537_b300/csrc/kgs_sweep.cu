@@ -169,10 +169,21 @@ __device__ __forceinline__ void pass_point(vec2_t<T>* pq, vec2_t<T>* uv, int N, 
 // (blockIdx.y = axis D-2, blockIdx.z = axis 0 for D = 3), so a thread finds its
 // point without divisions; blockIdx.x * blockDim.x + threadIdx.x runs over the
 // N/2 points of the pass's colour in the row.  32-bit indices when N^d < 2^31.
+//
+// In the slab schedule (pass_pair) the launches after a pair's first two are
+// programmatic dependent launches: a black slab pass B(k) reads the red slabs
+// k-1 .. k+1, which no launch still running writes (the red pass just before
+// it writes slab k-2), so it starts at once and overlaps that red pass's
+// tail; a red slab pass waits (griddepcontrol.wait) for the black pass just
+// before it, which itself started only after the red pass before it had
+// passed its own wait -- so the black slabs on both sides are complete.
+// Both instructions are no-ops in a plain launch.
 template <typename T, int D, int MODE, typename I>
 __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c,
                                                    int parity, int plane0)
 {
+    if (MODE != BLACK_FUSED) asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int kk = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * kk >= N) return;
     int i0 = 0, i1 = 0, rp = 0;
@@ -492,10 +503,21 @@ static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coe
     dim3 grid((unsigned)((hN + threads - 1) / threads), D == 2 ? (unsigned)planes : (D == 3 ? (unsigned)g.N : 1u),
               D == 3 ? (unsigned)planes : 1u);
     const int parity = (MODE == BLACK_FUSED) ? (red_parity(D) ^ 1) : red_parity(D);
-    if (g.M < ((int64_t)1 << 31))
-        pass_kernel<T, D, MODE, int32_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0);
-    else
-        pass_kernel<T, D, MODE, int64_t><<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0);
+    auto kern = g.M < ((int64_t)1 << 31) ? pass_kernel<T, D, MODE, int32_t> : pass_kernel<T, D, MODE, int64_t>;
+    if (!g.pdl) {
+        kern<<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, pq, uv, (int)g.N, c, parity, plane0);
 }
 
 // CTAs for the persistent pass: 148 SMs x b CTAs of 256 threads, b in 3..6
