@@ -446,6 +446,7 @@ def main():
     ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab and wave kernels)")
     ap.add_argument("--wave-lag", type=int, default=0, help="KGS_OPT_WAVE_LAG (wave kernel)")
     ap.add_argument("--wave-chunk", type=int, default=0, help="KGS_OPT_WAVE_CHUNK (wave kernel)")
+    ap.add_argument("--pdl", type=int, default=-1, help="KGS_OPT_PDL (-1: the library default)")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
     ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block"],
                     help="update order: the checkerboard (Algorithm 3), the lexicographic "
@@ -511,6 +512,9 @@ def main():
     if args.wave_chunk:
         from paper_2502_09537_b300.solver import KGS_OPT_WAVE_CHUNK
         s.set_option(KGS_OPT_WAVE_CHUNK, args.wave_chunk)
+    if args.pdl >= 0:
+        from paper_2502_09537_b300.solver import KGS_OPT_PDL
+        s.set_option(KGS_OPT_PDL, args.pdl)
     if args.order_mode:
         from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
         s.set_option(KGS_OPT_ORDER_MODE, args.order_mode)

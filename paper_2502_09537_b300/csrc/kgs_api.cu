@@ -56,6 +56,7 @@ struct kgs_solver {
     bool state_set = false;
     int sticky = 0;  // first CUDA error seen (cudaError_t), 0 if none
     int opt_kernel = 0, opt_graph = 1, opt_threads = 256;
+    int opt_pdl = 1;  // programmatic dependent launch of the plain colour passes
     int64_t opt_slab = 0;  // planes per slab of the slab kernel (0: from the L2 size)
     TileParams tile{};
     bool tile_set = false;  // tile parameters chosen by the caller
@@ -300,6 +301,7 @@ int pass_pair(kgs_solver* h, int red, cudaStream_t s)
         }
     }
     if (kernel_choice(h) != K_SLAB || h->dim < 2) {
+        g.pdl = g.pdl_wait = h->opt_pdl != 0;
         if (launch_pass<T>(g, BLACK_FUSED, pq, uv, *c, s) < 0 || launch_pass<T>(g, red, pq, uv, *c, s) < 0)
             return -1;
         h->launches += 2;
@@ -1002,6 +1004,11 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
         if (value != 128 && value != 256 && value != 512)
             return fail(KGS_ERR_ARG, "KGS_OPT_THREADS takes 128, 256 or 512");
         h->opt_threads = (int)value;
+        drop_graph(h);
+        return KGS_OK;
+    case KGS_OPT_PDL:
+        if (value < 0 || value > 1) return fail(KGS_ERR_ARG, "KGS_OPT_PDL takes 0 or 1");
+        h->opt_pdl = (int)value;
         drop_graph(h);
         return KGS_OK;
     case KGS_OPT_PPT:

@@ -22,6 +22,7 @@ struct Grid {
     int64_t plane0 = 0, planes = 0;
     bool split = false;  // state in the colour-split layout (below)
     bool pdl = false;    // launch with programmatic dependent launch (slab schedule)
+    bool pdl_wait = false;  // ... and make black passes wait for their predecessor too
 };
 
 // Colour-split state layout (a handle's state): the points of even coordinate

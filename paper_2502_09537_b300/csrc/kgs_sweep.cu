@@ -178,11 +178,12 @@ __device__ __forceinline__ void pass_point(vec2_t<T>* pq, vec2_t<T>* uv, int N, 
 // before it, which itself started only after the red pass before it had
 // passed its own wait -- so the black slabs on both sides are complete.
 // Both instructions are no-ops in a plain launch.
+// Outside the slab schedule (wait_all) every pass waits for the one before it.
 template <typename T, int D, int MODE, typename I>
 __global__ void __launch_bounds__(512) pass_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int N, Coef<T> c,
-                                                   int parity, int plane0)
+                                                   int parity, int plane0, int wait_all)
 {
-    if (MODE != BLACK_FUSED) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (MODE != BLACK_FUSED || wait_all) asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int kk = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * kk >= N) return;
@@ -504,8 +505,9 @@ static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coe
               D == 3 ? (unsigned)planes : 1u);
     const int parity = (MODE == BLACK_FUSED) ? (red_parity(D) ^ 1) : red_parity(D);
     auto kern = g.M < ((int64_t)1 << 31) ? pass_kernel<T, D, MODE, int32_t> : pass_kernel<T, D, MODE, int64_t>;
+    const int wait_all = g.pdl_wait ? 1 : 0;
     if (!g.pdl) {
-        kern<<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0);
+        kern<<<grid, threads, 0, s>>>(pq, uv, (int)g.N, c, parity, plane0, wait_all);
         return;
     }
     cudaLaunchConfig_t cfg = {};
@@ -517,7 +519,7 @@ static void launch_pass_t(const Grid& g, vec2_t<T>* pq, vec2_t<T>* uv, const Coe
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, pq, uv, (int)g.N, c, parity, plane0);
+    cudaLaunchKernelEx(&cfg, kern, pq, uv, (int)g.N, c, parity, plane0, wait_all);
 }
 
 // CTAs for the persistent pass: 148 SMs x b CTAs of 256 threads, b in 3..6

@@ -37,6 +37,7 @@ KGS_OPT_ORDER_MODE = 11
 KGS_OPT_TEST_BARRIER_STALL = 12
 KGS_OPT_WAVE_LAG = 13
 KGS_OPT_WAVE_CHUNK = 14
+KGS_OPT_PDL = 15
 KGS_ERR_TIMEOUT = -6
 
 # Every function the header declares, with its ctypes signature.

@@ -109,9 +109,20 @@ def test_kernel_variants_and_graphs_are_bitwise_equal():
     c = run_gpu(prob, st, 100, kernel=2)
     d = run_gpu(prob, st, 100, kernel=4)
     e = run_gpu(prob, st, 100, kernel=5)
-    for x, y, z, q, r in zip(a, b, c, d, e):
+    from paper_2502_09537_b300.solver import KGS_OPT_PDL
+    f = []
+    for graph in (1, 0):
+        with Solver.from_problem(prob) as s:
+            s.set_option(KGS_OPT_KERNEL, 1)
+            s.set_option(KGS_OPT_PDL, 1)
+            s.set_option(KGS_OPT_GRAPH, graph)
+            s.set_state(*copy_state(st))
+            s.step(60)
+            s.step(40)
+            f.append(s.get_state())
+    for x, y, z, q, r, f0, f1 in zip(a, b, c, d, e, f[0], f[1]):
         assert (np.array_equal(x, y) and np.array_equal(x, z) and np.array_equal(x, q)
-                and np.array_equal(x, r))
+                and np.array_equal(x, r) and np.array_equal(x, f0) and np.array_equal(x, f1))
 
 
 @pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
