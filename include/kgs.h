@@ -53,9 +53,10 @@ extern "C" {
 #define KGS_ERR_CUDA     -4  /* a CUDA call failed (also: no usable device) */
 #define KGS_ERR_STATE    -5  /* no state set yet */
 #define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out (a grid barrier of the persistent
-                               order launch or a dependency wait of the wave kernel did not
-                               complete within 2 s); the handle's state is lost and every later
-                               call on the handle returns this status */
+                               order launch, or a dependency wait of the wave kernel or of the
+                               lexicographic tile sweep, did not complete within 2 s); the
+                               handle's state is lost and every later call on the handle
+                               returns this status */
 #define KGS_ERR_RANGE    -7  /* size beyond what the call supports */
 
 /* memory kind of caller buffers */
@@ -86,22 +87,28 @@ extern "C" {
 #define KGS_OPT_TILE_LX      7  /* tile kernel: axis-0 planes per CTA */
 #define KGS_OPT_TILE_PASSES  8  /* tile kernel: colour passes per launch (= halo width), 1..8 */
 #define KGS_OPT_TILE_THREADS 9  /* tile kernel: threads per CTA (64, 128, 256, 512, 1024) */
-#define KGS_OPT_ORDER_MODE  11  /* update orders (kgs_set_order): 0 auto (default: mode 3, or
-                                   mode 1 if the second state buffer cannot be allocated), 1 one
+#define KGS_OPT_ORDER_MODE  11  /* update orders (kgs_set_order): 0 auto (default: mode 4 or 3,
+                                   or mode 1 if the second state buffer cannot be allocated), 1 one
                                    launch per level on the handle's state layout (a step captured
                                    in a CUDA graph), 2 every level of a step in one cooperative
                                    persistent launch with a grid barrier after each level
                                    (bounded: see KGS_ERR_TIMEOUT; kgs_step then waits for the
                                    device before returning), 3 one launch per level on a natural-
                                    order copy of the state (a second state buffer, allocated on
-                                   first use; each kgs_step call converts into it and back).  All
-                                   compute bitwise the same state. */
+                                   first use; each kgs_step call converts into it and back), 4 for
+                                   the lexicographic order or its reverse in 2D with N a multiple
+                                   of 32: on that copy, 32 x 32 tiles each swept by one warp along
+                                   its anti-diagonals, taken in a dependency-safe order in one
+                                   cooperative launch per half step (waits bounded: see
+                                   KGS_ERR_TIMEOUT; other orders and grids: as 3).  Auto takes 4
+                                   where it applies.  All compute bitwise the same state. */
 #define KGS_OPT_TEST_BARRIER_STALL 12  /* test hook: n > 0 makes every grid barrier of the
                                    persistent order launch wait for n CTAs that do not exist, and
-                                   every dependency wait of the wave kernel for n chunks that do
-                                   not exist, so they time out (after 2 s) and the handle reports
+                                   every dependency wait of the wave kernel and of the
+                                   lexicographic tile sweep for n chunks or tiles that do not
+                                   exist, so they time out (after 2 s) and the handle reports
                                    KGS_ERR_TIMEOUT (kgs_step for the order launch, which waits for
-                                   the device; the next synchronising call for the wave kernel);
+                                   the device; the next synchronising call for the others);
                                    0 (default) off.  For testing the timeout path only. */
 #define KGS_OPT_WAVE_LAG    13  /* wave kernel: slabs by which the red pass trails the black pass
                                    in the ticket order, 1 .. 64; 0 (default) = enough for the

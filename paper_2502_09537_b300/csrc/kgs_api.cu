@@ -78,7 +78,7 @@ struct kgs_solver {
     int64_t* olevels_dev = nullptr;    // level offsets on the device (persistent launches)
     int64_t omax_level = 0;            // points in the largest level
     OrderBarrier* obar = nullptr;      // grid barrier of the persistent launches
-    int opt_order_mode = 0;            // 0 auto, 1 levels on the split layout, 2 persistent, 3 levels on natural order
+    int opt_order_mode = 0;            // 0 auto, 1 levels on the split layout, 2 persistent, 3 levels on natural order, 4 lexicographic tiles
     int opt_stall = 0;                 // test hook: phantom CTAs every barrier waits for
     bool timed_out = false;            // a bounded device wait ran out: the state is lost
     // wave kernel (KGS_OPT_KERNEL 6): plan (0 not made, 1 usable, -1 not
@@ -90,6 +90,10 @@ struct kgs_solver {
     int* werr = nullptr;
     int opt_wave_lag = 0;
     int64_t opt_wave_chunk = 0;
+    // the order is the lexicographic one (1) or its reverse (-1), 0 otherwise;
+    // for grids lex_tiles_apply takes, the strip sweep's progress counters
+    int olex = 0;
+    unsigned* lsync = nullptr;
 };
 
 namespace {
@@ -233,6 +237,21 @@ int64_t slab_planes(const kgs_solver* h)
     return p < h->N ? p : h->N;
 }
 
+// The word a bounded device wait sets when it times out: pinned host memory
+// mapped into the device, so the host reads it without a copy.
+int ensure_err_word(kgs_solver* h)
+{
+    if (h->werr) return KGS_OK;
+    cudaError_t e = cudaHostAlloc(&h->werr, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->werr = nullptr;
+        return fail(KGS_ERR_OOM, "pinned error word: %s", cudaGetErrorString(e));
+    }
+    *(volatile int*)h->werr = 0;
+    return KGS_OK;
+}
+
 // The wave kernel's plan and buffers; returns 1 if it applies to the grid, 0
 // if not (the plain passes run instead), or a negative status.
 int ensure_wave(kgs_solver* h)
@@ -248,11 +267,7 @@ int ensure_wave(kgs_solver* h)
     cudaFree(h->wsync);
     h->wsync = nullptr;
     cudaError_t e = cudaMalloc(&h->wsync, (size_t)(2 + 2 * wp.ns) * sizeof(unsigned));
-    if (e == cudaSuccess && !h->werr) {
-        e = cudaHostAlloc(&h->werr, sizeof(int), cudaHostAllocMapped);
-        if (e == cudaSuccess) *(volatile int*)h->werr = 0;
-        else h->werr = nullptr;
-    }
+    if (e == cudaSuccess && ensure_err_word(h)) return KGS_ERR_OOM;
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA, "wave kernel buffers: %s",
@@ -449,6 +464,27 @@ int order_convert(kgs_solver* h, bool to_natural, cudaStream_t s)
 template <typename T>
 int step_in_order_levels(kgs_solver* h, int64_t nsteps, bool split, cudaStream_t s);
 
+// The lexicographic order (or its reverse) as a doacross sweep of row strips:
+// per step the base half in the order's direction, the adjoint half in the
+// other.
+template <typename T>
+int step_in_order_lex(kgs_solver* h, int64_t nsteps, cudaStream_t s)
+{
+    const Coef<T>* c;
+    if constexpr (sizeof(T) == 8) c = &h->cd;
+    else c = &h->cf;
+    vec2_t<T>* pq = (vec2_t<T>*)h->pqb[h->cur];
+    vec2_t<T>* uv = (vec2_t<T>*)h->uvb[h->cur];
+    const bool fwd = h->olex > 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        if (launch_lex_tiles<T>(fwd, RED_BASE, pq, uv, h->N, *c, h->lsync, h->werr, h->opt_stall, s) < 0 ||
+            launch_lex_tiles<T>(!fwd, RED_ADJ, pq, uv, h->N, *c, h->lsync, h->werr, h->opt_stall, s) < 0)
+            return cuda_fail(h, cudaGetLastError(), "lexicographic tile launch");
+        h->launches += 2;
+    }
+    return KGS_OK;
+}
+
 template <typename T>
 int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 {
@@ -456,7 +492,7 @@ int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
     // natural order suits the level schedules better: a level's points (an
     // anti-diagonal of the lexicographic order, say) find their neighbours
     // along the last axis in the cache sectors of their own values
-    bool natural = h->opt_order_mode == 3;
+    bool natural = h->opt_order_mode == 3 || h->opt_order_mode == 4;
     if (h->opt_order_mode == 0) {
         // without room for the copy, fall back to the levels on the split
         // layout, leaving the caller's last-error record as it was
@@ -469,10 +505,11 @@ int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
             memcpy(g_last_error, msg, sizeof msg);
         }
     }
+    const bool lex = natural && h->olex != 0 && h->lsync && (h->opt_order_mode == 0 || h->opt_order_mode == 4);
     if (natural) {
         int st = order_convert<T>(h, true, s);
         if (st) return st;
-        st = step_in_order_levels<T>(h, nsteps, false, s);
+        st = lex ? step_in_order_lex<T>(h, nsteps, s) : step_in_order_levels<T>(h, nsteps, false, s);
         const int st2 = order_convert<T>(h, false, s);
         return st ? st : st2;
     }
@@ -612,6 +649,8 @@ void free_all(kgs_solver* h)
     cudaFree(h->olevels_dev);
     cudaFree(h->obar);
     cudaFree(h->wsync);
+    cudaFree(h->lsync);
+    h->lsync = nullptr;
     if (h->werr) cudaFreeHost(h->werr);
     h->wsync = nullptr;
     h->werr = nullptr;
@@ -823,6 +862,7 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
     drop_graph(h);
+    h->olex = 0;
     if (!order) {
         cudaFree(h->olist);
         cudaFree(h->olevels_dev);
@@ -858,6 +898,25 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     h->omax_level = 0;
     for (size_t l = 0; l + 1 < off.size(); ++l) h->omax_level = std::max(h->omax_level, off[l + 1] - off[l]);
     h->olevels.swap(off);
+    // the lexicographic order or its reverse: the tile sweep applies
+    h->olex = 0;
+    bool fwd = true, bwd = true;
+    for (int64_t i = 0; i < h->M && (fwd || bwd); ++i) {
+        fwd = fwd && order[i] == i;
+        bwd = bwd && order[i] == h->M - 1 - i;
+    }
+    if ((fwd || bwd) && lex_tiles_apply(h->dim, h->N)) {
+        if (!h->lsync) {
+            e = cudaMalloc(&h->lsync, (size_t)(2 + h->N / 32) * sizeof(unsigned));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->lsync = nullptr;
+                return fail(KGS_ERR_OOM, "device memory for the lexicographic sweep");
+            }
+        }
+        if ((st = ensure_err_word(h))) return st;
+        h->olex = fwd ? 1 : -1;
+    }
     return KGS_OK;
 }
 
@@ -975,7 +1034,7 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
         h->opt_graph = (int)value;
         return KGS_OK;
     case KGS_OPT_ORDER_MODE:
-        if (value < 0 || value > 3) return fail(KGS_ERR_ARG, "KGS_OPT_ORDER_MODE takes 0 to 3");
+        if (value < 0 || value > 4) return fail(KGS_ERR_ARG, "KGS_OPT_ORDER_MODE takes 0 to 4");
         h->opt_order_mode = (int)value;
         return KGS_OK;
     case KGS_OPT_TEST_BARRIER_STALL:

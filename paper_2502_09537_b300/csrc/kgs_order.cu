@@ -278,6 +278,198 @@ int schedule_d(int64_t N, int64_t M, const int64_t* order, int32_t* level, int64
     return 0;
 }
 
+// ---------------------------------------------------- lexicographic strips --
+// The lexicographic order (Eq. order1) and its reverse in 2D, without one
+// launch per level: a doacross sweep.  One warp owns a strip of 32 rows of
+// the grid (natural order) and sweeps its columns with a skew of one column
+// per lane: at step t lane a updates row r_a, column j = t - a (forward;
+// mirrored for the reverse order: rows from the bottom, columns from the
+// right).  In the forward order a point's earlier neighbours are the one
+// above and the one to the left (new values), its later ones the one below
+// and the one to the right (old values); at step t the point above was
+// updated by lane a - 1 at step t - 1 (passed by a shuffle), the one to the
+// left by the same lane at step t - 1 (kept in registers), and the ones
+// below and to the right are not yet updated (read from memory).  The strip
+// above is another warp's: lane 0 reads its last row from memory once that
+// strip has published (release, every 8 steps) that it is at least 32 steps
+// ahead of the column (acquire).  Wrap-around neighbours are read from memory:
+// the left neighbour of column 0 is column N - 1 (still old), the right one
+// of column N - 1 is column 0 (new, written by the same lane), the row above
+// row 0 is row N - 1 (old: the last strip trails every other) and the row
+// below row N - 1 is row 0 (new).  So every point sees exactly the values of
+// the serial order, and with the same pointwise code and neighbour order as
+// level_point the result is bitwise the level schedule's.  Warps take strips
+// in ticket order (a strip waits only for the strip before it); the launch
+// is cooperative; a wait longer than kLexWaitNs sets the error words and the
+// warp leaves.
+constexpr int kLexStrip = 32;
+constexpr int kLexPublish = 8;  // steps between progress publications
+constexpr uint64_t kLexWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned lex_load_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// What one lane reads from memory for one step (all of it stable from the
+// step before, so it is loaded one step ahead): its point, the later
+// neighbours (next row, next column), and where they come from memory the
+// earlier ones (lane 0's previous row; the first column's wrap-around column).
+template <typename T> struct LexLoads {
+    vec2_t<T> a, e;      // the point's (P,Q) and (U,V)
+    vec2_t<T> nr, nc;    // (P,Q) of the next row's and the next column's neighbour
+    T nrU, ncU;          // their U
+    vec2_t<T> pr, pc;    // (P,Q) of the previous row's (lane 0) and previous column's (first column) neighbour
+    T prU, pcU;
+};
+
+template <typename T, bool FWD>
+__device__ __forceinline__ void lex_load(LexLoads<T>& L, const vec2_t<T>* pq, const vec2_t<T>* uv, int64_t N,
+                                         int64_t r, int64_t rprev, int64_t rnext, int k, int lane)
+{
+    const T* u = reinterpret_cast<const T*>(uv);
+    const int64_t j = FWD ? k : N - 1 - k;
+    const int64_t jm = j == 0 ? N - 1 : j - 1, jp = j == N - 1 ? 0 : j + 1;
+    const int64_t jprev = FWD ? jm : jp, jnext = FWD ? jp : jm;
+    L.a = pq[r * N + j];
+    L.e = uv[r * N + j];
+    L.nr = pq[rnext * N + j];
+    L.nrU = u[2 * (rnext * N + j)];
+    L.nc = pq[r * N + jnext];
+    L.ncU = u[2 * (r * N + jnext)];
+    if (lane == 0) {
+        L.pr = pq[rprev * N + j];
+        L.prU = u[2 * (rprev * N + j)];
+    }
+    if (k == 0) {
+        L.pc = pq[r * N + jprev];
+        L.pcU = u[2 * (r * N + jprev)];
+    }
+}
+
+template <typename T, int MODE, bool FWD>
+__global__ void __launch_bounds__(32) lex_strip_kernel(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, Coef<T> c,
+                                                       unsigned* sync, int* err, int stall)
+{
+    const int ns = (int)(N / kLexStrip);
+    const int lane = threadIdx.x;
+    const int steps = (int)N + kLexStrip - 1;
+    unsigned* derr = sync + 1;
+    unsigned* progress = sync + 2;  // steps strip s has completed, published
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = (int)atomicAdd(&sync[0], 1u);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= ns) break;
+        const int s = FWD ? t0 : ns - 1 - t0;        // this strip
+        const int sp = FWD ? s - 1 : s + 1;          // the strip updated before it (none at the ends)
+        const bool has_prev = sp >= 0 && sp < ns;
+        const int64_t r = FWD ? (int64_t)s * kLexStrip + lane : (int64_t)s * kLexStrip + kLexStrip - 1 - lane;
+        const int64_t rm = r == 0 ? N - 1 : r - 1, rp = r == N - 1 ? 0 : r + 1;  // rows above and below
+        const int64_t rprev = FWD ? rm : rp, rnext = FWD ? rp : rm;
+        T cP = 0, cQ = 0, cU = 0;  // this lane's last update (the previous column's new values)
+        LexLoads<T> cur, nxt;
+        int ok = 1;
+        for (int t = 0; t < steps; ++t) {
+            if (has_prev && (t % kLexPublish) == 0) {
+                // lane 0 reads the previous strip's last row at the columns of
+                // steps t .. t + kLexPublish (the last one prefetched); that
+                // strip's last lane reaches column x at its step x + 31
+                if (lane == 0) {
+                    const unsigned need = (unsigned)min(t + kLexPublish + kLexStrip, steps) + (unsigned)stall;
+                    const uint64_t w0 = globaltimer_ns();
+                    unsigned it = 0;
+                    while (lex_load_acquire(&progress[sp]) < need) {
+                        if (globaltimer_ns() - w0 > kLexWaitNs || ((++it & 63u) == 0u && *(volatile unsigned*)derr)) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                __syncwarp();  // carries lane 0's acquire to the warp
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+            }
+            const int k = t - lane;  // this lane's column index in sweep order
+            const bool active = k >= 0 && k < (int)N;
+            if (t == 0 || k == 0) {
+                if (active) lex_load<T, FWD>(cur, pq, uv, N, r, rprev, rnext, k, lane);
+            } else if (active) {
+                cur = nxt;
+            }
+            if (k + 1 >= 0 && k + 1 < (int)N && k + 1 > 0)
+                lex_load<T, FWD>(nxt, pq, uv, N, r, rprev, rnext, k + 1, lane);
+            // the point updated by lane - 1 at step t - 1 (row rprev, this column)
+            const T sP = __shfl_up_sync(0xffffffffu, cP, 1);
+            const T sQ = __shfl_up_sync(0xffffffffu, cQ, 1);
+            const T sU = __shfl_up_sync(0xffffffffu, cU, 1);
+            if (active) {
+                const T pP = lane == 0 ? cur.pr.x : sP, pQ = lane == 0 ? cur.pr.y : sQ, pU = lane == 0 ? cur.prU : sU;
+                const T lP = k == 0 ? cur.pc.x : cP, lQ = k == 0 ? cur.pc.y : cQ, lU = k == 0 ? cur.pcU : cU;
+                // the neighbours in level_point's order: axis 0 lower, upper; axis 1 lower, upper
+                T p[4], q[4], w[4];
+                p[0] = FWD ? pP : cur.nr.x;
+                q[0] = FWD ? pQ : cur.nr.y;
+                w[0] = FWD ? pU : cur.nrU;
+                p[1] = FWD ? cur.nr.x : pP;
+                q[1] = FWD ? cur.nr.y : pQ;
+                w[1] = FWD ? cur.nrU : pU;
+                p[2] = FWD ? lP : cur.nc.x;
+                q[2] = FWD ? lQ : cur.nc.y;
+                w[2] = FWD ? lU : cur.ncU;
+                p[3] = FWD ? cur.nc.x : lP;
+                q[3] = FWD ? cur.nc.y : lQ;
+                w[3] = FWD ? cur.ncU : lU;
+                vec2_t<T> a = cur.a, e = cur.e;
+                update_point<T, 2, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp),
+                                         a.x, a.y, e.x, e.y);
+                const int64_t j = FWD ? k : N - 1 - k;
+                pq[r * N + j] = a;
+                uv[r * N + j] = e;
+                cP = a.x;
+                cQ = a.y;
+                cU = e.x;
+            }
+            if ((t % kLexPublish) == kLexPublish - 1 || t == steps - 1) {
+                __syncwarp();  // the warp's stores precede lane 0's release
+                if (lane == 0)
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&progress[s]), "r"((unsigned)(t + 1))
+                                 : "memory");
+            }
+        }
+        if (!ok) {
+            if (lane == 0) {
+                *(volatile unsigned*)derr = 1u;
+                *(volatile int*)err = 1;
+            }
+            break;
+        }
+    }
+}
+
+template <typename T, int MODE, bool FWD>
+static int launch_lex_t(vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, const Coef<T>& c, unsigned* sync, int* err,
+                        int stall, cudaStream_t s)
+{
+    auto kern = lex_strip_kernel<T, MODE, FWD>;
+    int dev = 0, sms = 148, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLexStrip, 0) != cudaSuccess || per < 1) return -1;
+    const int64_t ns = N / kLexStrip;
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sms * per, ns);
+    if (cudaMemsetAsync(sync, 0, (size_t)(2 + ns) * sizeof(unsigned), s) != cudaSuccess) return -1;
+    Coef<T> cc = c;
+    int64_t n = N;
+    void* args[] = {&pq, &uv, &n, &cc, &sync, &err, &stall};
+    if (cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kLexStrip), args, 0, s) != cudaSuccess)
+        return -1;
+    return 1;
+}
+
 }  // namespace
 
 int order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels)
@@ -377,6 +569,28 @@ int launch_level_persistent(int dim, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t
     if (dim == 2) return launch_persistent_d<T, 2>(pq, uv, list, offsets, nlevels, max_level, N, c, bar, extra, s);
     return launch_persistent_d<T, 3>(pq, uv, list, offsets, nlevels, max_level, N, c, bar, extra, s);
 }
+
+bool lex_tiles_apply(int dim, int64_t N)
+{
+    return dim == 2 && N >= 2 * kLexStrip && N % kLexStrip == 0 && N <= 65534;
+}
+
+template <typename T>
+int launch_lex_tiles(bool forward, int mode, vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, const Coef<T>& c,
+                     unsigned* sync, int* err, int stall, cudaStream_t s)
+{
+    const bool base = mode == RED_BASE;
+    if (forward)
+        return base ? launch_lex_t<T, RED_BASE, true>(pq, uv, N, c, sync, err, stall, s)
+                    : launch_lex_t<T, RED_ADJ, true>(pq, uv, N, c, sync, err, stall, s);
+    return base ? launch_lex_t<T, RED_BASE, false>(pq, uv, N, c, sync, err, stall, s)
+                : launch_lex_t<T, RED_ADJ, false>(pq, uv, N, c, sync, err, stall, s);
+}
+
+template int launch_lex_tiles<double>(bool, int, vec2_t<double>*, vec2_t<double>*, int64_t, const Coef<double>&,
+                                      unsigned*, int*, int, cudaStream_t);
+template int launch_lex_tiles<float>(bool, int, vec2_t<float>*, vec2_t<float>*, int64_t, const Coef<float>&,
+                                     unsigned*, int*, int, cudaStream_t);
 
 template int launch_level_persistent<double>(int, vec2_t<double>*, vec2_t<double>*, const int64_t*,
                                              const int64_t*, int64_t, int64_t, int64_t, const Coef<double>&,

@@ -180,3 +180,60 @@ def test_barrier_timeout_is_reported_and_the_context_survives():
     from oracle import steps_order
     steps_order(prob, *want, orders.lexicographic(2, 16), 3)
     assert _rel(ref, want) <= FP64_BAR
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+@pytest.mark.parametrize("N,reverse", [(64, False), (96, False), (160, False), (64, True), (128, True)])
+def test_lexicographic_tiles_are_bitwise_the_level_schedule(N, reverse, precision):
+    """KGS_OPT_ORDER_MODE 4 (32 x 32 tiles, each swept by one warp along its
+    anti-diagonals, tiles taken in a dependency-safe order) computes the
+    lexicographic order and its reverse bitwise as the per-level launches do
+    (modes 3 and 1); auto takes the tiles."""
+    from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
+    prob = Problem(2, N, 11.0, 1.0, 0.8, 1.1, 0.9, 0.01)
+    st = random_state(prob, 2502_09537 + 130 + N + int(reverse))
+    order = orders.reverse_lexicographic(2, N) if reverse else orders.lexicographic(2, N)
+    out = {}
+    for mode in (4, 3, 1, 0):
+        with Solver.from_problem(prob, precision) as s:
+            s.set_option(KGS_OPT_ORDER_MODE, mode)
+            s.set_state(*_copy(st))
+            s.set_order(order)
+            s.step(4)
+            s.step(3)
+            out[mode] = s.get_state()
+    assert _bitwise(out[4], out[3]) and _bitwise(out[4], out[1]) and _bitwise(out[4], out[0])
+    if precision == KGS_FP64:
+        want = _copy(st)
+        from oracle import steps_order
+        steps_order(prob, *want, order, 7)
+        assert _rel(out[4], want) <= FP64_BAR
+
+
+def test_lexicographic_tile_wait_timeout_is_reported():
+    """A tile wait that cannot complete (the test hook makes every tile wait
+    for a neighbour tile count that is never reached) gives up after its 2 s
+    bound; the handle reports KGS_ERR_TIMEOUT at the next synchronising call
+    and from then on, and a new handle works."""
+    from paper_2502_09537_b300.solver import (KGS_ERR_TIMEOUT, KGS_OPT_ORDER_MODE,
+                                              KGS_OPT_TEST_BARRIER_STALL)
+    prob = Problem(2, 64, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
+    st = random_state(prob, 2502_09537 + 140)
+    with Solver.from_problem(prob) as s:
+        s.set_state(*_copy(st))
+        s.set_order(orders.lexicographic(2, 64))
+        s.set_option(KGS_OPT_ORDER_MODE, 4)
+        s.set_option(KGS_OPT_TEST_BARRIER_STALL, 1)
+        s.step(1)
+        with pytest.raises(KGSError) as ei:
+            s.get_state()
+        assert ei.value.status == KGS_ERR_TIMEOUT
+        with pytest.raises(KGSError) as ei:
+            s.step(1)
+        assert ei.value.status == KGS_ERR_TIMEOUT
+    a, _ = _gpu(prob, st, orders.lexicographic(2, 64), [2])
+    b, _ = _gpu(prob, st, None, [2])   # the checkerboard, for contrast
+    want = _copy(st)
+    from oracle import steps_order
+    steps_order(prob, *want, orders.lexicographic(2, 64), 2)
+    assert _rel(a, want) <= FP64_BAR and not _bitwise(a, b)
