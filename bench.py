@@ -72,6 +72,15 @@ NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 23.94e6,       # pass_kernel_fp64_kgs2
                ("3d", "fp64"): 8 * (471.38e6 + 228.27e6),  # pass_kernel_fp64_kgs3d_N256.md, x8 points
                ("3d", "fp32"): 1.8822e9 + 1.0328e9}        # pass_kernel_fp32_kgs3d_N512.md
 
+def traffic_of(args):
+    """DRAM bytes per pass launch from the ncu captures above: only for the
+    launches they were taken on (the default one-per-pass kernel on the
+    workload's full grid, checkerboard order); None otherwise."""
+    if args.order != "checkerboard" or args.kernel not in (0, 1) or args.grid_n:
+        return None
+    return NCU_TRAFFIC.get((args.workload, args.precision))
+
+
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), 148 SMs, 2032 MHz maximum SM
 # clock -> 2 x 2 x 148 x 2.032e9 = 1.203e12 flop/s.
@@ -585,8 +594,7 @@ def main():
         peak = FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": (NCU_TRAFFIC.get((args.workload, args.precision))
-                            if args.order == "checkerboard" else None),
+                "traffic": traffic_of(args),
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
                 "probe_tflops": 2 * fma_rate / 1e12,
                 "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r and 1/(1+r^2) run on the integer pipes)",
@@ -602,7 +610,7 @@ def main():
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+                "traffic": traffic_of(args),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
 
     line = {
