@@ -68,9 +68,9 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 # DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
 # ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
 # the kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 23.94e6,       # pass_kernel_fp64_kgs2d_N2048.md
-               ("3d", "fp64"): 8 * (471.38e6 + 228.27e6),  # pass_kernel_fp64_kgs3d_N256.md, x8 points
-               ("3d", "fp32"): 1.8822e9 + 1.0328e9}        # pass_kernel_fp32_kgs3d_N512.md
+NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 23.11e6,     # pass_kernel_fp64_kgs2d_N2048.md (RED_FUSED)
+               ("3d", "fp64"): 3.7656e9 + 2.1085e9,    # pass_kernel_fp64_kgs3d_N256.md (512^3 launch)
+               ("3d", "fp32"): 1.8822e9 + 1.0321e9}    # pass_kernel_fp32_kgs3d_N512.md (512^3 launch)
 
 def traffic_of(args):
     """DRAM bytes per pass launch from the ncu captures above: only for the
