@@ -17,9 +17,11 @@
 // list.  Each instance i may run its own number of steps n_i; pass g of its
 // run is applied while g <= 2 n_i and skipped after.  The
 // launches of a kgs_batch_step_each call are captured once into a CUDA graph
-// and replayed while the instance set and step counts stay the same.  The
-// FP64 and FP32 launch sequences run on two streams forked from the caller's
-// (the first bound by the FP64 pipe, the second by DRAM) and join at the end.  Every
+// and replayed while the instance set and step counts stay the same.  Each
+// (precision, dimension) list's launch sequence runs on its own stream forked
+// from the caller's and joined at the end: the lists hold disjoint instances,
+// so their passes overlap (FP64 passes bound by the FP64 pipe beside FP32
+// passes bound by DRAM, and one list's pass filling another's tail).  Every
 // point update is the code of a solo run with the same neighbour order, so
 // each instance's state is bitwise that of stepping it alone.
 #include <algorithm>
@@ -192,8 +194,8 @@ struct kgs_batch {
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;  // step counts the graph was captured for
     cudaStream_t capture_stream = nullptr;
-    cudaStream_t side = nullptr;            // second stream: the FP32 passes
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t side[6] = {};              // streams of the lists after the first
+    cudaEvent_t fork = nullptr, join[6] = {};
     int64_t launches = 0;
     int sticky = 0;
     double* scratch = nullptr;  // invariants partials
@@ -390,15 +392,6 @@ int launch_list_pass(kgs_batch* b, const kgs_batch::DevList& dl, const HostList<
     return r;
 }
 
-template <typename T>
-int launch_pass_all(kgs_batch* b, const HostList<T> (&L)[3], int64_t g, cudaStream_t s)
-{
-    kgs_batch::DevList* dl = b->lists[sizeof(T) == 8 ? 0 : 1];
-    int r = launch_list_pass<T, 1>(b, dl[0], L[0], g, s);
-    if (!r) r = launch_list_pass<T, 2>(b, dl[1], L[1], g, s);
-    if (!r) r = launch_list_pass<T, 3>(b, dl[2], L[2], g, s);
-    return r;
-}
 
 int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
 {
@@ -406,11 +399,7 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     HostList<float> l32[3];
     build_lists(b, nsteps, l64);
     build_lists(b, nsteps, l32);
-    int64_t c64 = 0, c32 = 0, nmax = 0;
-    for (int d = 0; d < 3; ++d) {
-        c64 += l64[d].chunks;
-        c32 += l32[d].chunks;
-    }
+    int64_t nmax = 0;
     for (size_t i = 0; i < b->inst.size(); ++i)
         if (b->inst[i].live) nmax = std::max(nmax, nsteps[i]);
     if (nmax == 0) return KGS_OK;
@@ -430,33 +419,53 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
         if (!st) st = upload_list(b, b->lists[1][d], l32[d], s);
     }
     if (st) return st;
-    // FP64 passes (bound by the FP64 pipe) on the caller's stream, FP32 passes
-    // (bound by DRAM) on a second stream forked from it, so the two precisions
-    // overlap; the side stream joins back before the call's work completes.
-    const bool both = c64 && c32;
-    if (both && !b->side) {
-        cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
-        if (e != cudaSuccess) return bcuda(b, e, "side stream");
+    // Every non-empty list on its own stream: the first on the caller's, the
+    // others on side streams forked from it; all join back before the call's
+    // work completes.
+    const int64_t lchunks[6] = {l64[0].chunks, l64[1].chunks, l64[2].chunks,
+                                l32[0].chunks, l32[1].chunks, l32[2].chunks};
+    int nactive = 0;
+    for (int k = 0; k < 6; ++k) nactive += lchunks[k] > 0;
+    if (nactive > 1 && !b->fork) {
+        cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return bcuda(b, e, "side streams");
     }
     auto issue = [&](cudaStream_t main) -> int {
-        cudaStream_t s32 = main;
-        if (both) {
+        cudaStream_t ls[6];
+        bool first = true;
+        if (nactive > 1) {
             cudaError_t e = cudaEventRecord(b->fork, main);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
             if (e != cudaSuccess) return bcuda(b, e, "fork");
-            s32 = b->side;
+        }
+        for (int k = 0; k < 6; ++k) {
+            ls[k] = main;
+            if (!lchunks[k]) continue;
+            if (first) {
+                first = false;
+                continue;
+            }
+            cudaError_t e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+            if (e != cudaSuccess) return bcuda(b, e, "fork");
+            ls[k] = b->side[k];
         }
         int r = KGS_OK;
         for (int64_t g = 0; g < passes && !r; ++g) {
-            r = launch_pass_all<double>(b, l64, g, main);
-            if (!r) r = launch_pass_all<float>(b, l32, g, s32);
+            r = launch_list_pass<double, 1>(b, b->lists[0][0], l64[0], g, ls[0]);
+            if (!r) r = launch_list_pass<double, 2>(b, b->lists[0][1], l64[1], g, ls[1]);
+            if (!r) r = launch_list_pass<double, 3>(b, b->lists[0][2], l64[2], g, ls[2]);
+            if (!r) r = launch_list_pass<float, 1>(b, b->lists[1][0], l32[0], g, ls[3]);
+            if (!r) r = launch_list_pass<float, 2>(b, b->lists[1][1], l32[1], g, ls[4]);
+            if (!r) r = launch_list_pass<float, 3>(b, b->lists[1][2], l32[2], g, ls[5]);
         }
         if (r) return r;
-        if (both) {
-            cudaError_t e = cudaEventRecord(b->join, b->side);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(main, b->join, 0);
+        for (int k = 0; k < 6; ++k) {
+            if (ls[k] == main) continue;
+            cudaError_t e = cudaEventRecord(b->join[k], ls[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(main, b->join[k], 0);
             if (e != cudaSuccess) return bcuda(b, e, "join");
         }
         return KGS_OK;
@@ -795,9 +804,11 @@ void kgs_batch_destroy(kgs_batch_handle b)
         BatchDevGuard guard(b->device);
         drop_batch_graph(b);
         if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-        if (b->side) cudaStreamDestroy(b->side);
+        for (int k = 0; k < 6; ++k) {
+            if (b->side[k]) cudaStreamDestroy(b->side[k]);
+            if (b->join[k]) cudaEventDestroy(b->join[k]);
+        }
         if (b->fork) cudaEventDestroy(b->fork);
-        if (b->join) cudaEventDestroy(b->join);
         cudaFree(b->arena);
         for (auto& row : b->lists)
             for (auto& dl : row) {
