@@ -142,6 +142,8 @@ void compute_coef(kgs_solver* h)
 
 void drop_graph(kgs_solver* h)
 {
+    // a replay of either graph may still be queued: let it finish first
+    if (h->graph || h->ograph) cudaDeviceSynchronize();
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -644,6 +646,7 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 
 void free_all(kgs_solver* h)
 {
+    cudaDeviceSynchronize();  // no queued work may still use what is freed below
     drop_graph(h);
     cudaFree(h->olist);
     cudaFree(h->olevels_dev);

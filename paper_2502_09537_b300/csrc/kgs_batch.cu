@@ -193,6 +193,10 @@ struct kgs_batch {
     int use_graph = 1;
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;  // step counts the graph was captured for
+    cudaEvent_t graph_ev = nullptr;  // recorded after each launch of the graph
+    // graphs replaced while a launch of theirs may still run: destroyed once
+    // the event recorded after that launch has completed
+    std::vector<std::pair<cudaGraphExec_t, cudaEvent_t>> retired;
     cudaStream_t capture_stream = nullptr;
     cudaStream_t side[6] = {};              // streams of the lists after the first
     cudaEvent_t fork = nullptr, join[6] = {};
@@ -236,11 +240,47 @@ int bcheck(kgs_batch* b)
     return KGS_OK;
 }
 
+// Destroy the retired graphs whose last launch has completed (all of them,
+// waiting if need be, when wait is set).
+void reap_graphs(kgs_batch* b, bool wait)
+{
+    size_t keep = 0;
+    for (auto& r : b->retired) {
+        if (wait) cudaEventSynchronize(r.second);
+        if (cudaEventQuery(r.second) == cudaSuccess) {
+            cudaGraphExecDestroy(r.first);
+            cudaEventDestroy(r.second);
+        } else {
+            b->retired[keep++] = r;
+        }
+    }
+    b->retired.resize(keep);
+    cudaGetLastError();  // a pending query is not an error
+}
+
 void drop_batch_graph(kgs_batch* b)
 {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph) {
+        if (b->graph_ev) {
+            b->retired.emplace_back(b->graph, b->graph_ev);
+            b->graph_ev = nullptr;
+        } else {
+            cudaGraphExecDestroy(b->graph);  // never launched
+        }
+    }
     b->graph = nullptr;
     b->graph_key.clear();
+    reap_graphs(b, b->retired.size() > 16);
+}
+
+// Launch the batch graph on s and record its event after the launch.
+cudaError_t launch_batch_graph(kgs_batch* b, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->graph_ev) e = cudaEventCreateWithFlags(&b->graph_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->graph_ev, s);
+    return e;
 }
 
 // first-fit placement in the arena (256-byte aligned ranges)
@@ -407,8 +447,9 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
     std::vector<int64_t> key(nsteps, nsteps + b->inst.size());
     for (size_t i = 0; i < b->inst.size(); ++i)
         if (!b->inst[i].live) key[i] = -1;
+    reap_graphs(b, false);
     if (b->use_graph && b->graph && key == b->graph_key) {
-        cudaError_t e = cudaGraphLaunch(b->graph, s);
+        cudaError_t e = launch_batch_graph(b, s);
         if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
         b->launches += b->graph_launches;
         return KGS_OK;
@@ -496,7 +537,7 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
         return bcuda(b, e, "cudaGraphInstantiate");
     }
     b->graph_key = key;
-    e = cudaGraphLaunch(b->graph, s);
+    e = launch_batch_graph(b, s);
     if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
     b->launches += b->graph_launches;
     return KGS_OK;
@@ -802,7 +843,10 @@ void kgs_batch_destroy(kgs_batch_handle b)
     if (!b) return;
     {
         BatchDevGuard guard(b->device);
+        cudaDeviceSynchronize();  // no queued work may still use what is freed below
         drop_batch_graph(b);
+        reap_graphs(b, true);
+        if (b->graph_ev) cudaEventDestroy(b->graph_ev);
         if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
         for (int k = 0; k < 6; ++k) {
             if (b->side[k]) cudaStreamDestroy(b->side[k]);

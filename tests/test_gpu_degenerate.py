@@ -122,3 +122,25 @@ def test_gamma_zero_decouples_psi_from_u(dim, N, precision):
     # and the runs did move
     assert not np.array_equal(ra[0], a[0]) and not np.array_equal(ra[2], a[2])
     assert math.isfinite(float(np.abs(ra[0]).max()))
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+def test_changing_tau_between_graph_replays(precision):
+    """kgs_set_tau between two runs long enough to replay the captured step
+    graph: the second run uses the new tau (bitwise what a fresh handle with
+    that tau computes from the same state), not the graph's old constants."""
+    prob = Problem(2, 64, 9.0, 1.1, 0.9, 1.2, 0.8, 0.01)
+    st = random_state(prob, 2502_09537 + 250, 0.6)
+    with Solver.from_problem(prob, precision) as s:
+        s.set_state(*copy_state(st))
+        s.step(40)
+        mid = s.get_state()
+        s.set_tau(0.004)
+        s.step(40)
+        got = s.get_state()
+    want, _ = run(prob._replace(tau=0.004), mid, 40, precision)
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+    first, _ = run(prob, st, 40, precision)
+    for x, y in zip(mid, first):
+        assert np.array_equal(x, y)
