@@ -54,7 +54,7 @@ extern "C" {
 #define KGS_ERR_STATE    -5  /* no state set yet */
 #define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out (a grid barrier of the persistent
                                order launch, or a dependency wait of the wave kernel or of the
-                               lexicographic tile sweep, did not complete within 2 s); the
+                               lexicographic sweep, did not complete within 2 s); the
                                handle's state is lost and every later call on the handle
                                returns this status */
 #define KGS_ERR_RANGE    -7  /* size beyond what the call supports */
@@ -97,15 +97,16 @@ extern "C" {
                                    order copy of the state (a second state buffer, allocated on
                                    first use; each kgs_step call converts into it and back), 4 for
                                    the lexicographic order or its reverse in 2D with N a multiple
-                                   of 32: on that copy, 32 x 32 tiles each swept by one warp along
-                                   its anti-diagonals, taken in a dependency-safe order in one
-                                   cooperative launch per half step (waits bounded: see
-                                   KGS_ERR_TIMEOUT; other orders and grids: as 3).  Auto takes 4
-                                   where it applies.  All compute bitwise the same state. */
+                                   of 32: on that copy, a doacross sweep in one cooperative launch
+                                   per half step -- one warp per strip of 32 rows, its lanes one
+                                   column apart, each strip trailing the one before it (waits
+                                   bounded: see KGS_ERR_TIMEOUT; other orders and grids: as 3).
+                                   Auto takes 4 where it applies.  All compute bitwise the same
+                                   state. */
 #define KGS_OPT_TEST_BARRIER_STALL 12  /* test hook: n > 0 makes every grid barrier of the
                                    persistent order launch wait for n CTAs that do not exist, and
                                    every dependency wait of the wave kernel and of the
-                                   lexicographic tile sweep for n chunks or tiles that do not
+                                   lexicographic sweep for n chunks or steps that do not
                                    exist, so they time out (after 2 s) and the handle reports
                                    KGS_ERR_TIMEOUT (kgs_step for the order launch, which waits for
                                    the device; the next synchronising call for the others);

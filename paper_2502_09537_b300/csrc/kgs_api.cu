@@ -78,7 +78,7 @@ struct kgs_solver {
     int64_t* olevels_dev = nullptr;    // level offsets on the device (persistent launches)
     int64_t omax_level = 0;            // points in the largest level
     OrderBarrier* obar = nullptr;      // grid barrier of the persistent launches
-    int opt_order_mode = 0;            // 0 auto, 1 levels on the split layout, 2 persistent, 3 levels on natural order, 4 lexicographic tiles
+    int opt_order_mode = 0;            // 0 auto, 1 levels on the split layout, 2 persistent, 3 levels on natural order, 4 lexicographic sweep
     int opt_stall = 0;                 // test hook: phantom CTAs every barrier waits for
     bool timed_out = false;            // a bounded device wait ran out: the state is lost
     // wave kernel (KGS_OPT_KERNEL 6): plan (0 not made, 1 usable, -1 not
@@ -91,7 +91,7 @@ struct kgs_solver {
     int opt_wave_lag = 0;
     int64_t opt_wave_chunk = 0;
     // the order is the lexicographic one (1) or its reverse (-1), 0 otherwise;
-    // for grids lex_tiles_apply takes, the strip sweep's progress counters
+    // for grids lex_sweep_applies takes, the strip sweep's progress counters
     int olex = 0;
     unsigned* lsync = nullptr;
 };
@@ -479,9 +479,9 @@ int step_in_order_lex(kgs_solver* h, int64_t nsteps, cudaStream_t s)
     vec2_t<T>* uv = (vec2_t<T>*)h->uvb[h->cur];
     const bool fwd = h->olex > 0;
     for (int64_t k = 0; k < nsteps; ++k) {
-        if (launch_lex_tiles<T>(fwd, RED_BASE, pq, uv, h->N, *c, h->lsync, h->werr, h->opt_stall, s) < 0 ||
-            launch_lex_tiles<T>(!fwd, RED_ADJ, pq, uv, h->N, *c, h->lsync, h->werr, h->opt_stall, s) < 0)
-            return cuda_fail(h, cudaGetLastError(), "lexicographic tile launch");
+        if (launch_lex_sweep<T>(fwd, RED_BASE, pq, uv, h->N, *c, h->lsync, h->werr, h->opt_stall, s) < 0 ||
+            launch_lex_sweep<T>(!fwd, RED_ADJ, pq, uv, h->N, *c, h->lsync, h->werr, h->opt_stall, s) < 0)
+            return cuda_fail(h, cudaGetLastError(), "lexicographic sweep launch");
         h->launches += 2;
     }
     return KGS_OK;
@@ -908,7 +908,7 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
         fwd = fwd && order[i] == i;
         bwd = bwd && order[i] == h->M - 1 - i;
     }
-    if ((fwd || bwd) && lex_tiles_apply(h->dim, h->N)) {
+    if ((fwd || bwd) && lex_sweep_applies(h->dim, h->N)) {
         if (!h->lsync) {
             e = cudaMalloc(&h->lsync, (size_t)(2 + h->N / 32) * sizeof(unsigned));
             if (e != cudaSuccess) {

@@ -129,15 +129,15 @@ int launch_level_persistent(int dim, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t
 // The lexicographic order (and its reverse) in 2D as a doacross sweep
 // (kgs_order.cu): one warp per strip of 32 rows, its lanes skewed by one
 // column, each strip trailing the one before it; on natural vec2 order.
-// lex_tiles_apply: whether the grid qualifies (dim 2, N a multiple of 32,
-// N >= 64).  launch_lex_tiles: one half step (forward = increasing lex order)
+// lex_sweep_applies: whether the grid qualifies (dim 2, N a multiple of 32,
+// N >= 64).  launch_lex_sweep: one half step (forward = increasing lex order)
 // of MODE RED_BASE or RED_ADJ; sync: 2 + N/32 unsigned words on the device
 // (zeroed by the launcher), err: a word set to 1 if a wait timed out (2 s;
 // stall > 0 makes every wait need that many extra steps, which tests the
 // timeout).  Returns 1, or -1 if the launch failed.
-bool lex_tiles_apply(int dim, int64_t N);
+bool lex_sweep_applies(int dim, int64_t N);
 template <typename T>
-int launch_lex_tiles(bool forward, int mode, vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, const Coef<T>& c,
+int launch_lex_sweep(bool forward, int mode, vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, const Coef<T>& c,
                      unsigned* sync, int* err, int stall, cudaStream_t s);
 
 // Layout conversion (kgs_layout.cu): one float64 field <-> one component of a

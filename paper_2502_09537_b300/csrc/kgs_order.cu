@@ -570,13 +570,13 @@ int launch_level_persistent(int dim, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t
     return launch_persistent_d<T, 3>(pq, uv, list, offsets, nlevels, max_level, N, c, bar, extra, s);
 }
 
-bool lex_tiles_apply(int dim, int64_t N)
+bool lex_sweep_applies(int dim, int64_t N)
 {
     return dim == 2 && N >= 2 * kLexStrip && N % kLexStrip == 0 && N <= 65534;
 }
 
 template <typename T>
-int launch_lex_tiles(bool forward, int mode, vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, const Coef<T>& c,
+int launch_lex_sweep(bool forward, int mode, vec2_t<T>* pq, vec2_t<T>* uv, int64_t N, const Coef<T>& c,
                      unsigned* sync, int* err, int stall, cudaStream_t s)
 {
     const bool base = mode == RED_BASE;
@@ -587,9 +587,9 @@ int launch_lex_tiles(bool forward, int mode, vec2_t<T>* pq, vec2_t<T>* uv, int64
                 : launch_lex_t<T, RED_ADJ, false>(pq, uv, N, c, sync, err, stall, s);
 }
 
-template int launch_lex_tiles<double>(bool, int, vec2_t<double>*, vec2_t<double>*, int64_t, const Coef<double>&,
+template int launch_lex_sweep<double>(bool, int, vec2_t<double>*, vec2_t<double>*, int64_t, const Coef<double>&,
                                       unsigned*, int*, int, cudaStream_t);
-template int launch_lex_tiles<float>(bool, int, vec2_t<float>*, vec2_t<float>*, int64_t, const Coef<float>&,
+template int launch_lex_sweep<float>(bool, int, vec2_t<float>*, vec2_t<float>*, int64_t, const Coef<float>&,
                                      unsigned*, int*, int, cudaStream_t);
 
 template int launch_level_persistent<double>(int, vec2_t<double>*, vec2_t<double>*, const int64_t*,

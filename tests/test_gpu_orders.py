@@ -184,11 +184,11 @@ def test_barrier_timeout_is_reported_and_the_context_survives():
 
 @pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
 @pytest.mark.parametrize("N,reverse", [(64, False), (96, False), (160, False), (64, True), (128, True)])
-def test_lexicographic_tiles_are_bitwise_the_level_schedule(N, reverse, precision):
-    """KGS_OPT_ORDER_MODE 4 (32 x 32 tiles, each swept by one warp along its
-    anti-diagonals, tiles taken in a dependency-safe order) computes the
+def test_lexicographic_sweep_is_bitwise_the_level_schedule(N, reverse, precision):
+    """KGS_OPT_ORDER_MODE 4 (a doacross sweep: one warp per strip of 32 rows,
+    lanes one column apart, strips chained by progress counters) computes the
     lexicographic order and its reverse bitwise as the per-level launches do
-    (modes 3 and 1); auto takes the tiles."""
+    (modes 3 and 1); auto takes the sweep."""
     from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
     prob = Problem(2, N, 11.0, 1.0, 0.8, 1.1, 0.9, 0.01)
     st = random_state(prob, 2502_09537 + 130 + N + int(reverse))
@@ -210,11 +210,11 @@ def test_lexicographic_tiles_are_bitwise_the_level_schedule(N, reverse, precisio
         assert _rel(out[4], want) <= FP64_BAR
 
 
-def test_lexicographic_tile_wait_timeout_is_reported():
-    """A tile wait that cannot complete (the test hook makes every tile wait
-    for a neighbour tile count that is never reached) gives up after its 2 s
-    bound; the handle reports KGS_ERR_TIMEOUT at the next synchronising call
-    and from then on, and a new handle works."""
+def test_lexicographic_sweep_wait_timeout_is_reported():
+    """A strip's wait that cannot complete (the test hook makes every strip
+    wait for progress the strip before it never reaches) gives up after its
+    2 s bound; the handle reports KGS_ERR_TIMEOUT at the next synchronising
+    call and from then on, and a new handle works."""
     from paper_2502_09537_b300.solver import (KGS_ERR_TIMEOUT, KGS_OPT_ORDER_MODE,
                                               KGS_OPT_TEST_BARRIER_STALL)
     prob = Problem(2, 64, 8.0, 1.0, 1.0, 1.0, 1.0, 0.01)
