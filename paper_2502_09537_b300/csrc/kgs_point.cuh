@@ -435,11 +435,21 @@ template <typename T> __device__ __forceinline__ T uv_src(const Coef<T>& c, T BS
 
 // One (U,V) update, the implicit midpoint rule of the last two equations of
 // Eq. scheme1:  a = U + (s/2) V,  dV = t' - 2A' a,  V' = V + dV,  U' = a + (s/2) V'.
-template <typename T> __device__ __forceinline__ void uv_step(const Coef<T>& c, T t, T& U, T& V)
+// V + dV correctly rounded on the integer pipes (a two-term exact sum): the
+// same value as the FP64 addition, for passes whose integer pipes have room.
+__device__ __forceinline__ double add_int(double a, double b)
+{
+    const double v[2] = {a, b};
+    return nsum<2>(v);
+}
+__device__ __forceinline__ float add_int(float a, float b) { return add_(a, b); }
+
+template <typename T, bool INT_ADD = false>
+__device__ __forceinline__ void uv_step(const Coef<T>& c, T t, T& U, T& V)
 {
     const T a = fma_(c.hs, V, U);
     const T dV = fma_(-c.twoAp, a, t);
-    V = add_(V, dV);
+    V = INT_ADD ? add_int(V, dV) : add_(V, dV);
     U = fma_(c.hs, V, a);
 }
 
@@ -456,7 +466,10 @@ enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3 };
 // Update one point of the pass's colour in registers.  bSP, bSQ = beta S_P,
 // beta S_Q and BSU = B' S_U from the neighbour sums above (neighbours are of
 // the other colour and fixed for the pass).
-template <typename T, int D, int MODE>
+// INT_ADD: the fused red pass forms its two V additions on the integer pipes
+// (bitwise the same values); the default takes it in 1D/2D, where that
+// pass's integer pipes have room.
+template <typename T, int D, int MODE, bool INT_ADD = (D <= 2)>
 __device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T BSU,
                                              T& P, T& Q, T& U, T& V)
 {
@@ -472,11 +485,14 @@ __device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T B
         uv_step(c, t, U, V);
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // adjoint Psi with U^{n+1}
     } else if (MODE == RED_FUSED) {
-        uv_step(c, uv_src(c, BSU, P, Q), U, V);      // adjoint (U,V) with |Psi^n|^2
+        // in 1D/2D this pass's integer pipes have room (one Psi weight, sums
+        // of 2d <= 4 terms): its two V additions can run there (in 3D its
+        // 6-term sums fill them already)
+        uv_step<T, INT_ADD>(c, uv_src(c, BSU, P, Q), U, V);  // adjoint (U,V) with |Psi^n|^2
         const PsiPrep<T> pp = psi_prep<T, D>(c, U);
         psi_apply(pp, bSP, bSQ, P, Q);              // adjoint Psi with U^{n+1}
         psi_apply(pp, bSP, bSQ, P, Q);              // next base Psi: same U, same r
-        uv_step(c, uv_src(c, BSU, P, Q), U, V);      // next base (U,V)
+        uv_step<T, INT_ADD>(c, uv_src(c, BSU, P, Q), U, V);  // next base (U,V)
     } else {  // RED_ADJ
         uv_step(c, uv_src(c, BSU, P, Q), U, V);
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);
