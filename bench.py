@@ -49,12 +49,12 @@ def flops_per_point_update(dim: int) -> float:
     source 5 (|Psi|^2 3, E'|Psi|^2 + B'S_U 2), one (U,V) step 7 (three FMAs
     and the V addition).  Black pass: 2 prepares + 2 applies + 1 source + 2
     steps = 47 flops (25 instructions); red pass: 1 prepare + 2 applies + 2
-    sources + 2 steps = 50 (27), of which in 1D/2D the two V additions run on
-    the integer pipes: 48 (25).  A point-update is the mean: 47.5 in 1D/2D,
-    48.5 in 3D.  The neighbour sums, beta S, B' S_U, 2r and 1/(1 + r^2) run
-    on the integer pipes too."""
+    sources + 2 steps = 50 (27), of which the V additions run on the integer
+    pipes, both in 1D/2D (48 flops, 25 instructions), one in 3D (49, 26).  A
+    point-update is the mean: 47.5 in 1D/2D, 48 in 3D.  The neighbour sums,
+    beta S, B' S_U, 2r and 1/(1 + r^2) run on the integer pipes too."""
     black = 2 * 2 + 2 * 12 + 5 + 2 * 7
-    red = 2 + 2 * 12 + 2 * 5 + 2 * 7 - (2 if dim <= 2 else 0)
+    red = 2 + 2 * 12 + 2 * 5 + 2 * 7 - (2 if dim <= 2 else 1)
     return (black + red) / 2
 
 
@@ -71,7 +71,7 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 # ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
 # the kernels as they are now; None where no capture of the current kernel exists.
 NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 25.74e6,     # pass_kernel_fp64_kgs2d_N2048.md (RED_FUSED)
-               ("3d", "fp64"): 3.7656e9 + 2.1085e9,    # pass_kernel_fp64_kgs3d_N256.md (512^3 launch)
+               ("3d", "fp64"): 3.7645e9 + 2.1086e9,    # pass_kernel_fp64_kgs3d_N256.md (512^3 launch)
                ("3d", "fp32"): 1.8822e9 + 1.0321e9}    # pass_kernel_fp32_kgs3d_N512.md (512^3 launch)
 
 def traffic_of(args):
@@ -295,7 +295,7 @@ def run_batch(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
-                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and, in 1D/2D, the red pass's V additions run on the integer pipes)"}
+                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and the red pass's V additions -- both in 1D/2D, one in 3D -- run on the integer pipes)"}
     else:
         achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6400.0),
@@ -599,7 +599,7 @@ def main():
                 "traffic": traffic_of(args),
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
                 "probe_tflops": 2 * fma_rate / 1e12,
-                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and, in 1D/2D, the red pass's V additions run on the integer pipes)",
+                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and the red pass's V additions -- both in 1D/2D, one in 3D -- run on the integer pipes)",
                 "flops_per_point_update": fpu,
                 "algorithmic_flops_per_point_update": algorithmic_flops_per_point_update(prob.dim),
                 "algorithmic_tflops": upd_per_launch * algorithmic_flops_per_point_update(prob.dim)

@@ -125,8 +125,8 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int pa
     vec2_t<T> a = in.pq[own];
     T U = u[own], V = u[2 * half + own];
     // FP64 V additions here: under the batch kernels' 64-register cap the
-    // integer form spills (measured 1.3% slower on the batch workload)
-    update_point<T, D, MODE, false>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta),
+    // integer form spills (measured 1.3% slower on the batch workload, 2D)
+    update_point<T, D, MODE, false, false>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta),
                                     nsum_scaled(w, in.coef.Bp), a.x, a.y, U, V);
     in.pq[own] = a;
     u[own] = U;

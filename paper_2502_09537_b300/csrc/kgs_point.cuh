@@ -466,10 +466,11 @@ enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3 };
 // Update one point of the pass's colour in registers.  bSP, bSQ = beta S_P,
 // beta S_Q and BSU = B' S_U from the neighbour sums above (neighbours are of
 // the other colour and fixed for the pass).
-// INT_ADD: the fused red pass forms its two V additions on the integer pipes
-// (bitwise the same values); the default takes it in 1D/2D, where that
-// pass's integer pipes have room.
-template <typename T, int D, int MODE, bool INT_ADD = (D <= 2)>
+// INT_ADD, INT_ADD1: the fused red pass forms both of its V additions, or
+// only the first, on the integer pipes (bitwise the same values): both in
+// 1D/2D, where that pass's integer pipes have room, the first in 3D, where
+// its 6-term sums leave room for one (measured: two slow it down).
+template <typename T, int D, int MODE, bool INT_ADD = (D <= 2), bool INT_ADD1 = true>
 __device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T BSU,
                                              T& P, T& Q, T& U, T& V)
 {
@@ -485,10 +486,9 @@ __device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T B
         uv_step(c, t, U, V);
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);  // adjoint Psi with U^{n+1}
     } else if (MODE == RED_FUSED) {
-        // in 1D/2D this pass's integer pipes have room (one Psi weight, sums
-        // of 2d <= 4 terms): its two V additions can run there (in 3D its
-        // 6-term sums fill them already)
-        uv_step<T, INT_ADD>(c, uv_src(c, BSU, P, Q), U, V);  // adjoint (U,V) with |Psi^n|^2
+        // this pass's integer pipes have room (one Psi weight): its V
+        // additions can run there, both in 1D/2D, one in 3D
+        uv_step<T, INT_ADD || INT_ADD1>(c, uv_src(c, BSU, P, Q), U, V);  // adjoint (U,V) with |Psi^n|^2
         const PsiPrep<T> pp = psi_prep<T, D>(c, U);
         psi_apply(pp, bSP, bSQ, P, Q);              // adjoint Psi with U^{n+1}
         psi_apply(pp, bSP, bSQ, P, Q);              // next base Psi: same U, same r
