@@ -114,13 +114,13 @@ extern "C" {
 #define KGS_OPT_WAVE_LAG    13  /* wave kernel: slabs by which the red pass trails the black pass
                                    in the ticket order, 1 .. 64; 0 (default) = enough for the
                                    chunks in flight (2 + CTAs / (2 chunks per slab)) */
+#define KGS_OPT_WAVE_CHUNK  14  /* wave kernel: points of a colour per chunk (rounded down to
+                                   whole rows, at least one), 1 .. 2^24; 0 (default) = 2048 */
 #define KGS_OPT_PDL         15  /* 1 (default): launch the one-per-pass colour passes (kernel 1)
                                    with programmatic dependent launch, each waiting in the kernel
                                    for the one before, so a pass's launch overlaps the previous
                                    pass's tail (+0.3% on the 2D FP64 workload); 0 plain launches.
                                    Bitwise the same state either way. */
-#define KGS_OPT_WAVE_CHUNK  14  /* wave kernel: points of a colour per chunk (rounded down to
-                                   whole rows, at least one), 1 .. 2^24; 0 (default) = 2048 */
 #define KGS_OPT_SLAB_PLANES 10  /* slab and wave kernels: axis-0 planes per slab, 1 .. N (the
                                    wave kernel takes the largest divisor of N not above it);
                                    0 (default) picks about a quarter of the L2 cache's bytes per
