@@ -211,6 +211,56 @@ void orc_steps_order(int dim, int64_t N, double L, double kappa1, double kappa2,
 }
 
 /* 1 if point i is red: its 1-based index sum is odd (Algorithm 3). */
+/* nsteps DP-AVF2 steps with a separate update order for Psi (order_psi) and
+ * for (U,V) (order_uv), in place.  The remark after Eq. dp-avf-kj-adj allows
+ * different orders per variable; Algorithm 1 states the pointwise procedure
+ * for one common order.  Reading: a point's Psi update reads U only at that
+ * point and its (U,V) update reads Psi only at that point, so Algorithm 1's
+ * per-point interleaving over one order equals two whole sweeps -- every Psi
+ * update in the order (with U^n), then every (U,V) update in the order (with
+ * |Psi^{n+1}|^2) -- and per-variable orders are those two sweeps in their own
+ * orders.  The adjoint half reverses both: the (U,V) sweep over order_uv
+ * reversed (with the |Psi|^2 the base half left), then the Psi sweep over
+ * order_psi reversed (with U^{n+1}).  With order_psi == order_uv this is
+ * orc_steps_order exactly (the same updates with the same inputs). */
+static void orc_psi_sweep(const orc_ctx* c, const int64_t* order, int forward, double* P, double* Q,
+                          const double* U)
+{
+    for (int64_t k = 0; k < c->M; ++k) {
+        const int64_t i = order[forward ? k : c->M - 1 - k];
+        orc_psi_update(c, i, P, Q, U[i], U[i]);
+    }
+}
+
+static void orc_uv_sweep(const orc_ctx* c, const int64_t* order, int forward, const double* P,
+                         const double* Q, double* U, double* V)
+{
+    for (int64_t k = 0; k < c->M; ++k) {
+        const int64_t i = order[forward ? k : c->M - 1 - k];
+        orc_uv_update(c, i, U, V, orc_rho(P, Q, i));
+    }
+}
+
+void orc_steps_orders2(int dim, int64_t N, double L, double kappa1, double kappa2,
+                       double mu, double gamma, double tau,
+                       double* P, double* Q, double* U, double* V,
+                       const int64_t* order_psi, const int64_t* order_uv, int64_t nsteps, int mut)
+{
+    orc_ctx c;
+    orc_setup(&c, dim, N, L, kappa1, kappa2, mu, gamma, tau / 2.0, mut);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        orc_psi_sweep(&c, order_psi, 1, P, Q, U);      /* base half: Psi with U^n */
+        orc_uv_sweep(&c, order_uv, 1, P, Q, U, V);     /* then (U,V) with |Psi^{n+1}|^2 */
+        if (c.mut & ORC_MUT_NO_ADJ_SWAP) {             /* planted: adjoint keeps Psi first */
+            orc_psi_sweep(&c, order_psi, 0, P, Q, U);
+            orc_uv_sweep(&c, order_uv, 0, P, Q, U, V);
+        } else {
+            orc_uv_sweep(&c, order_uv, 0, P, Q, U, V);  /* adjoint: (U,V) with |Psi^n|^2 */
+            orc_psi_sweep(&c, order_psi, 0, P, Q, U);   /* then Psi with U^{n+1} */
+        }
+    }
+}
+
 static int orc_is_red(const orc_ctx* c, int64_t i)
 {
     int64_t s = 0;

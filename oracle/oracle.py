@@ -42,6 +42,9 @@ def _load():
         lib.orc_steps_order.argtypes = common + [ctypes.c_double, _dp, _dp, _dp, _dp,
                                                  _i64p, ctypes.c_int64, ctypes.c_int]
         lib.orc_steps_order.restype = None
+        lib.orc_steps_orders2.argtypes = common + [ctypes.c_double, _dp, _dp, _dp, _dp,
+                                                   _i64p, _i64p, ctypes.c_int64, ctypes.c_int]
+        lib.orc_steps_orders2.restype = None
         lib.orc_steps_checkerboard.argtypes = common + [ctypes.c_double, _dp, _dp, _dp, _dp,
                                                         ctypes.c_int64]
         lib.orc_steps_checkerboard.restype = None
@@ -86,6 +89,26 @@ def steps_order(prob, P, Q, U, V, order, nsteps: int, mut: int = 0) -> None:
         raise ValueError("order must be a permutation of 0..N^d-1")
     _load().orc_steps_order(dim, N, L, k1, k2, mu, gamma, tau, _ptr(P), _ptr(Q), _ptr(U),
                             _ptr(V), order.ctypes.data_as(_i64p), nsteps, mut)
+
+
+def _permutation(order, M):
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    if order.shape != (M,) or not np.array_equal(np.sort(order), np.arange(M)):
+        raise ValueError("order must be a permutation of 0..N^d-1")
+    return order
+
+
+def steps_orders2(prob, P, Q, U, V, order_psi, order_uv, nsteps: int, mut: int = 0) -> None:
+    """Advance (P,Q,U,V) in place by nsteps DP-AVF2 steps with one update order
+    for Psi and another for (U,V) (the remark after Eq. dp-avf-kj-adj): per
+    step the Psi sweep in order_psi, the (U,V) sweep in order_uv, then both
+    reversed, (U,V) first (orc_steps_orders2 states the reading)."""
+    dim, N, L, k1, k2, mu, gamma, tau = prob
+    _check_state(dim, N, (P, Q, U, V))
+    op = _permutation(order_psi, N ** dim)
+    ou = _permutation(order_uv, N ** dim)
+    _load().orc_steps_orders2(dim, N, L, k1, k2, mu, gamma, tau, _ptr(P), _ptr(Q), _ptr(U), _ptr(V),
+                              op.ctypes.data_as(_i64p), ou.ctypes.data_as(_i64p), nsteps, mut)
 
 
 def steps_checkerboard(prob, P, Q, U, V, nsteps: int) -> None:
