@@ -459,9 +459,11 @@ def main():
     ap.add_argument("--wave-chunk", type=int, default=0, help="KGS_OPT_WAVE_CHUNK (wave kernel)")
     ap.add_argument("--pdl", type=int, default=-1, help="KGS_OPT_PDL (-1: the library default)")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (tuning)")
-    ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block"],
+    ap.add_argument("--order", default="checkerboard", choices=["checkerboard", "lex", "block", "lex-rev"],
                     help="update order: the checkerboard (Algorithm 3), the lexicographic "
-                         "wavefront (Eq. order1) or Algorithm 2's block order (2D, 16 blocks)")
+                         "wavefront (Eq. order1), Algorithm 2's block order (2D, 16 blocks), or "
+                         "lex-rev: Psi in the lexicographic order and (U,V) in its reverse "
+                         "(per-variable orders, kgs_set_orders)")
     ap.add_argument("--order-mode", type=int, default=0,
                     help="KGS_OPT_ORDER_MODE for a general order: 0 auto, 1 one launch per level "
                          "(colour-split layout), 2 one persistent launch per step, 3 one launch per "
@@ -529,7 +531,10 @@ def main():
     if args.order_mode:
         from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
         s.set_option(KGS_OPT_ORDER_MODE, args.order_mode)
-    if args.order != "checkerboard":
+    if args.order == "lex-rev":
+        from paper_2502_09537_b300 import orders
+        s.set_orders(orders.lexicographic(prob.dim, prob.N), orders.reverse_lexicographic(prob.dim, prob.N))
+    elif args.order != "checkerboard":
         from paper_2502_09537_b300 import orders
         s.set_order(orders.lexicographic(prob.dim, prob.N) if args.order == "lex"
                     else orders.block_split_2d(prob.N, 16))

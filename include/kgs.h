@@ -203,10 +203,26 @@ int kgs_step(kgs_handle h, int64_t nsteps, void* stream);
  * a permutation; the handle's order is unchanged), KGS_ERR_OOM (host or
  * device memory) or KGS_ERR_CUDA.
  *
- * kgs_order_levels: the number of levels of the handle's current order (2
- * for the checkerboard). */
+ * kgs_set_orders: one update order for Psi (order_psi) and another for (U,V)
+ * (order_uv), both N^d int64 on the host, copied (the remark after Eq.
+ * dp-avf-kj-adj: the variables may follow different orders).  A point's Psi
+ * update reads U only at that point and its (U,V) update reads Psi only at
+ * that point, so Algorithm 1's per-point procedure over one order is two whole
+ * sweeps, and with two orders each half step is: base -- Psi over order_psi
+ * (with U^n), then (U,V) over order_uv (with |Psi^{n+1}|^2); adjoint --
+ * (U,V) over order_uv reversed, then Psi over order_psi reversed (with
+ * U^{n+1}).  Equal orders give exactly kgs_set_order's scheme.  These orders
+ * run as per-level launches (KGS_OPT_ORDER_MODE 1 or 3; modes 2 and 4 apply
+ * to one common order only).  Both pointers are required; kgs_set_order
+ * (also with NULL) returns to one order.  Returns as kgs_set_order; on
+ * KGS_ERR_ARG for order_uv nothing changes.
+ *
+ * kgs_order_levels: the number of level launches per half step of the
+ * handle's current order(s) (2 for the checkerboard; with two orders, the
+ * sum of their levels). */
 int kgs_order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels);
 int kgs_set_order(kgs_handle h, const int64_t* order);
+int kgs_set_orders(kgs_handle h, const int64_t* order_psi, const int64_t* order_uv);
 int kgs_order_levels(kgs_handle h, int64_t* nlevels);
 
 /* Discrete invariants of the current state, computed on the device in float64

@@ -72,6 +72,10 @@ struct kgs_solver {
     // by level on the device, level offsets on the host; empty = checkerboard
     int64_t* olist = nullptr;
     std::vector<int64_t> olevels;
+    // a separate order for (U,V) (kgs_set_orders): its level list and offsets;
+    // null = the same order as Psi (Algorithm 1's per-point procedure)
+    int64_t* olist_uv = nullptr;
+    std::vector<int64_t> olevels_uv;
     cudaGraphExec_t ograph = nullptr;  // one step of the order, captured
     int ograph_buf = -1;
     bool ograph_split = true;          // the layout the order graph was captured for
@@ -392,25 +396,44 @@ int ensure_graph(kgs_solver* h)
 
 // One DP-AVF2 step in the handle's order: the base half over the levels in
 // increasing order, the adjoint half in decreasing order.
+// One sweep over an order's levels (upward = the order's direction) in mode m.
 template <typename T>
-int order_step(kgs_solver* h, bool split, cudaStream_t s)
+int order_sweep(kgs_solver* h, const int64_t* list, const std::vector<int64_t>& levels, bool upward, int m,
+                bool split, cudaStream_t s)
 {
     const Coef<T>* c;
     if constexpr (sizeof(T) == 8) c = &h->cd;
     else c = &h->cf;
     vec2_t<T>* pq = (vec2_t<T>*)h->pqb[h->cur];
     vec2_t<T>* uv = (vec2_t<T>*)h->uvb[h->cur];
-    const int64_t nl = (int64_t)h->olevels.size() - 1;
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int64_t k = 0; k < nl; ++k) {
-            const int64_t l = pass == 0 ? k : nl - 1 - k;
-            const int64_t o = h->olevels[(size_t)l], n = h->olevels[(size_t)l + 1] - o;
-            const int r = launch_level<T>(h->dim, pass == 0 ? RED_BASE : RED_ADJ, pq, uv, h->olist + o, n,
-                                          h->N, *c, split, s);
-            if (r < 0) return -1;
-            h->launches += r;
-        }
+    const int64_t nl = (int64_t)levels.size() - 1;
+    for (int64_t k = 0; k < nl; ++k) {
+        const int64_t l = upward ? k : nl - 1 - k;
+        const int64_t o = levels[(size_t)l], n = levels[(size_t)l + 1] - o;
+        const int r = launch_level<T>(h->dim, m, pq, uv, list + o, n, h->N, *c, split, s);
+        if (r < 0) return -1;
+        h->launches += r;
     }
+    return 0;
+}
+
+// One step in the handle's order(s): the base half up the levels, the adjoint
+// half down; with a separate (U,V) order, each half is two sweeps (base: Psi
+// in its order, then (U,V) in its order; adjoint: (U,V), then Psi, both
+// reversed) -- with one order the same arithmetic as the per-point form.
+template <typename T>
+int order_step(kgs_solver* h, bool split, cudaStream_t s)
+{
+    if (!h->olist_uv)
+        return order_sweep<T>(h, h->olist, h->olevels, true, RED_BASE, split, s) ||
+                       order_sweep<T>(h, h->olist, h->olevels, false, RED_ADJ, split, s)
+                   ? -1
+                   : 0;
+    if (order_sweep<T>(h, h->olist, h->olevels, true, PSI_HALF, split, s) ||
+        order_sweep<T>(h, h->olist_uv, h->olevels_uv, true, UV_HALF, split, s) ||
+        order_sweep<T>(h, h->olist_uv, h->olevels_uv, false, UV_HALF, split, s) ||
+        order_sweep<T>(h, h->olist, h->olevels, false, PSI_HALF, split, s))
+        return -1;
     return 0;
 }
 
@@ -490,7 +513,7 @@ int step_in_order_lex(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 template <typename T>
 int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
 {
-    if (h->opt_order_mode == 2) return step_in_order_persistent<T>(h, nsteps, s);
+    if (h->opt_order_mode == 2 && !h->olist_uv) return step_in_order_persistent<T>(h, nsteps, s);
     // natural order suits the level schedules better: a level's points (an
     // anti-diagonal of the lexicographic order, say) find their neighbours
     // along the last axis in the cache sectors of their own values
@@ -507,7 +530,8 @@ int step_in_order(kgs_solver* h, int64_t nsteps, cudaStream_t s)
             memcpy(g_last_error, msg, sizeof msg);
         }
     }
-    const bool lex = natural && h->olex != 0 && h->lsync && (h->opt_order_mode == 0 || h->opt_order_mode == 4);
+    const bool lex = natural && h->olex != 0 && h->lsync && !h->olist_uv &&
+                     (h->opt_order_mode == 0 || h->opt_order_mode == 4);
     if (natural) {
         int st = order_convert<T>(h, true, s);
         if (st) return st;
@@ -554,6 +578,7 @@ int step_in_order_levels(kgs_solver* h, int64_t nsteps, bool split, cudaStream_t
         }
         int64_t per = 0;
         for (size_t l = 0; l + 1 < h->olevels.size(); ++l) per += h->olevels[l + 1] > h->olevels[l];
+        for (size_t l = 0; l + 1 < h->olevels_uv.size(); ++l) per += h->olevels_uv[l + 1] > h->olevels_uv[l];
         for (int64_t k = 0; k < nsteps; ++k) {
             cudaError_t e = cudaGraphLaunch(h->ograph, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
@@ -649,6 +674,7 @@ void free_all(kgs_solver* h)
     cudaDeviceSynchronize();  // no queued work may still use what is freed below
     drop_graph(h);
     cudaFree(h->olist);
+    cudaFree(h->olist_uv);
     cudaFree(h->olevels_dev);
     cudaFree(h->obar);
     cudaFree(h->wsync);
@@ -866,6 +892,9 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
     drop_graph(h);
     h->olex = 0;
+    cudaFree(h->olist_uv);
+    h->olist_uv = nullptr;
+    h->olevels_uv.clear();
     if (!order) {
         cudaFree(h->olist);
         cudaFree(h->olevels_dev);
@@ -923,12 +952,40 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     return KGS_OK;
 }
 
+int kgs_set_orders(kgs_handle h, const int64_t* order_psi, const int64_t* order_uv)
+{
+    int st = check_handle(h);
+    if (st) return st;
+    if (!order_psi || !order_uv) return fail(KGS_ERR_ARG, "both orders are required (kgs_set_order resets)");
+    // validate the (U,V) order before changing anything
+    std::vector<int64_t> list, off;
+    st = order_lists(h->dim, h->N, order_uv, list, off);
+    if (st == -3) return fail(KGS_ERR_OOM, "host memory for the order schedule");
+    if (st) return fail(KGS_ERR_ARG, "order_uv is not a permutation of 0 .. N^d - 1");
+    if ((st = kgs_set_order(h, order_psi))) return st;  // clears any earlier (U,V) order
+    if (std::equal(order_psi, order_psi + h->M, order_uv)) return KGS_OK;  // one common order
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+    cudaError_t e = cudaMalloc(&h->olist_uv, (size_t)h->M * sizeof(int64_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->olist_uv = nullptr;
+        return fail(KGS_ERR_OOM, "device memory for the (U,V) order (%lld points)", (long long)h->M);
+    }
+    e = cudaMemcpy(h->olist_uv, list.data(), (size_t)h->M * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "order upload");
+    h->olevels_uv.swap(off);
+    h->olex = 0;  // the lexicographic sweep runs one common order only
+    return KGS_OK;
+}
+
 int kgs_order_levels(kgs_handle h, int64_t* nlevels)
 {
     int st = check_handle(h);
     if (st) return st;
     if (!nlevels) return fail(KGS_ERR_ARG, "NULL output");
-    *nlevels = h->olevels.empty() ? 2 : (int64_t)h->olevels.size() - 1;
+    *nlevels = h->olevels.empty() ? 2 : (int64_t)h->olevels.size() - 1 + (int64_t)h->olevels_uv.size() -
+                                            (h->olevels_uv.empty() ? 0 : 1);
     return KGS_OK;
 }
 

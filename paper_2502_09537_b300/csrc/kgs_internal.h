@@ -101,8 +101,9 @@ int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<
 // level (stable in order position), as packed coordinates (the last axis in
 // the lowest bits, 63 / 31 / 21 bits per axis in 1 / 2 / 3 dimensions), and
 // the level offsets (nlevels + 1).
-// launch_level: one level's points, MODE RED_BASE (base half) or RED_ADJ
-// (adjoint half), on the colour-split layout (split) or on natural vec2 order;
+// launch_level: one level's points, MODE RED_BASE (base half), RED_ADJ
+// (adjoint half), PSI_HALF or UV_HALF (one variable's update alone, for
+// per-variable orders), on the colour-split layout (split) or on natural vec2 order;
 // returns 1, 0 for an empty level, -1 if the launch failed.
 int order_schedule(int dim, int64_t N, const int64_t* order, int32_t* level, int64_t* nlevels);
 int order_lists(int dim, int64_t N, const int64_t* order, std::vector<int64_t>& list,

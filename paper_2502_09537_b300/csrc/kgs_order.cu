@@ -520,11 +520,15 @@ int launch_level(int dim, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t*
     const bool small = count < 148 * 256;
     const int threads = small ? 64 : 256;
     const unsigned blocks = (unsigned)((count + threads - 1) / threads);
-    const bool base = mode == RED_BASE;
     cudaError_t e = cudaSuccess;
-#define KGS_LEVEL_S(DD, SP)                                                                            \
-    if (base) e = launch_level_pdl<T, DD, RED_BASE, SP>(blocks, threads, s, pq, uv, list, count, N, c, small); \
-    else e = launch_level_pdl<T, DD, RED_ADJ, SP>(blocks, threads, s, pq, uv, list, count, N, c, small);
+#define KGS_LEVEL_M(DD, SP, MM) e = launch_level_pdl<T, DD, MM, SP>(blocks, threads, s, pq, uv, list, count, N, c, small);
+#define KGS_LEVEL_S(DD, SP)                                   \
+    switch (mode) {                                           \
+    case RED_BASE: KGS_LEVEL_M(DD, SP, RED_BASE) break;       \
+    case RED_ADJ: KGS_LEVEL_M(DD, SP, RED_ADJ) break;         \
+    case PSI_HALF: KGS_LEVEL_M(DD, SP, PSI_HALF) break;       \
+    default: KGS_LEVEL_M(DD, SP, UV_HALF) break;              \
+    }
 #define KGS_LEVEL(DD)                 \
     if (split) { KGS_LEVEL_S(DD, true) } \
     else { KGS_LEVEL_S(DD, false) }
@@ -533,6 +537,7 @@ int launch_level(int dim, int mode, vec2_t<T>* pq, vec2_t<T>* uv, const int64_t*
     else { KGS_LEVEL(3) }
 #undef KGS_LEVEL
 #undef KGS_LEVEL_S
+#undef KGS_LEVEL_M
     return e == cudaSuccess ? 1 : -1;
 }
 

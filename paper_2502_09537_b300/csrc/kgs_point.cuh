@@ -461,7 +461,12 @@ __device__ __forceinline__ void uv_step(const Coef<T>& c, T t, T& U, T& V)
 //   RED_BASE, (BLACK_FUSED, RED_FUSED) x (n-1), BLACK_FUSED, RED_ADJ.
 // RED_FUSED computes exactly RED_ADJ followed by RED_BASE, so a run split
 // into several calls gives bitwise the same state.
-enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3 };
+enum PassMode { RED_BASE = 0, BLACK_FUSED = 1, RED_FUSED = 2, RED_ADJ = 3, PSI_HALF = 4, UV_HALF = 5 };
+// PSI_HALF and UV_HALF: one variable's update alone, for update orders that
+// differ per variable (kgs_set_orders): the Psi update with the point's
+// current U, the (U,V) update with the point's current |Psi|^2.  RED_BASE is
+// PSI_HALF then UV_HALF at a point, RED_ADJ is UV_HALF then PSI_HALF, with
+// the same arithmetic.
 
 // Update one point of the pass's colour in registers.  bSP, bSQ = beta S_P,
 // beta S_Q and BSU = B' S_U from the neighbour sums above (neighbours are of
@@ -493,9 +498,13 @@ __device__ __forceinline__ void update_point(const Coef<T>& c, T bSP, T bSQ, T B
         psi_apply(pp, bSP, bSQ, P, Q);              // adjoint Psi with U^{n+1}
         psi_apply(pp, bSP, bSQ, P, Q);              // next base Psi: same U, same r
         uv_step<T, INT_ADD>(c, uv_src(c, BSU, P, Q), U, V);  // next base (U,V)
-    } else {  // RED_ADJ
+    } else if (MODE == RED_ADJ) {
         uv_step(c, uv_src(c, BSU, P, Q), U, V);
         psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);
+    } else if (MODE == PSI_HALF) {
+        psi_apply(psi_prep<T, D>(c, U), bSP, bSQ, P, Q);
+    } else {  // UV_HALF
+        uv_step(c, uv_src(c, BSU, P, Q), U, V);
     }
 }
 

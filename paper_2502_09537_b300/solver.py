@@ -60,6 +60,7 @@ SIGNATURES = {
     "kgs_destroy": (None, [_vp]),
     "kgs_order_schedule": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _vp, ctypes.POINTER(_c_int64)]),
     "kgs_set_order": (ctypes.c_int, [_vp, _vp]),
+    "kgs_set_orders": (ctypes.c_int, [_vp, _vp, _vp]),
     "kgs_order_levels": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64)]),
     "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kgs_last_error": (ctypes.c_char_p, []),
@@ -214,6 +215,15 @@ class Solver:
             return
         o = _order_array(order, self.N ** self.dim)
         _check(self._lib.kgs_set_order(self._h, o.ctypes.data))
+
+    def set_orders(self, order_psi, order_uv):
+        """One update order for Psi and another for (U,V) (kgs_set_orders):
+        each half step sweeps the variables in their own orders, (U,V) first
+        and both reversed in the adjoint half."""
+        M = self.N ** self.dim
+        op = _order_array(order_psi, M)
+        ou = _order_array(order_uv, M)
+        _check(self._lib.kgs_set_orders(self._h, op.ctypes.data, ou.ctypes.data))
 
     def order_levels(self) -> int:
         """Parallel levels per half step of the current order (2 for the checkerboard)."""

@@ -237,3 +237,76 @@ def test_lexicographic_sweep_wait_timeout_is_reported():
     from oracle import steps_order
     steps_order(prob, *want, orders.lexicographic(2, 64), 2)
     assert _rel(a, want) <= FP64_BAR and not _bitwise(a, b)
+
+
+def _orders2_pair(dim, N, k):
+    lex, rev = orders.lexicographic(dim, N), orders.reverse_lexicographic(dim, N)
+    cb = orders.checkerboard(dim, N)
+    r1 = orders.random_order(dim, N, 2502_09537 + 401 + dim)
+    return [(lex, rev), (cb, r1), (rev, cb)][k]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("dim,N,k", [(1, 40, 0), (2, 18, 0), (2, 18, 1), (2, 64, 2), (3, 8, 1)])
+def test_per_variable_orders_match_oracle(orc, dim, N, k, mode):
+    """kgs_set_orders (one order for Psi, another for (U,V)) against the
+    oracle's two-sweep form (float64 bar 1e-12), per-level launches on the
+    colour-split layout (mode 1) and on the natural-order copy (3, auto)."""
+    from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
+    prob = Problem(dim, N, 9.0, 1.1, 0.9, 1.2, 0.8, 0.01)
+    st = random_state(prob, 2502_09537 + 410 + dim + k, 0.6)
+    op, ou = _orders2_pair(dim, N, k)
+    with Solver.from_problem(prob) as s:
+        s.set_option(KGS_OPT_ORDER_MODE, mode)
+        s.set_state(*_copy(st))
+        s.set_orders(op, ou)
+        s.step(7)
+        s.step(5)
+        got = s.get_state()
+    want = _copy(st)
+    orc.steps_orders2(prob, *want, op, ou, 12)
+    assert _rel(got, want) <= FP64_BAR
+
+
+@pytest.mark.parametrize("precision", [KGS_FP64, KGS_FP32])
+def test_equal_per_variable_orders_are_bitwise_one_order(precision):
+    """With the same order for both variables the two-sweep form is the
+    per-point form: bitwise kgs_set_order's result; kgs_set_order afterwards
+    returns to one order."""
+    prob = Problem(2, 22, 9.0, 1.1, 0.9, 1.2, 0.8, 0.01)
+    st = random_state(prob, 2502_09537 + 420, 0.6)
+    o = orders.random_order(2, 22, 2502_09537 + 421)
+    one, _ = _gpu(prob, st, o, [6, 4], precision)
+    with Solver.from_problem(prob, precision) as s:
+        s.set_state(*_copy(st))
+        s.set_orders(o, o)
+        s.step(6)
+        s.step(4)
+        same = s.get_state()
+    assert _bitwise(one, same)
+    op, ou = _orders2_pair(2, 22, 1)
+    with Solver.from_problem(prob, precision) as s:
+        s.set_state(*_copy(st))
+        s.set_orders(op, ou)
+        assert s.order_levels() > 2
+        s.set_order(o)
+        s.step(6)
+        s.step(4)
+        reset = s.get_state()
+    assert _bitwise(one, reset)
+
+
+def test_energy_conserved_with_per_variable_orders():
+    prob = Problem(2, 24, 8.0, 1.0, 1.1, 0.9, 1.2, 0.02)
+    st = random_state(prob, 2502_09537 + 430, 0.6)
+    op, ou = _orders2_pair(2, 24, 0)
+    with Solver.from_problem(prob) as s:
+        s.set_state(*_copy(st))
+        s.set_orders(op, ou)
+        E0, S0, _ = s.invariants()
+        worst = 0.0
+        for _ in range(5):
+            s.step(200)
+            E, S, _ = s.invariants()
+            worst = max(worst, abs(E - E0) / max(S0, S))
+    assert worst <= 1e-13, worst
