@@ -138,7 +138,10 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int pa
 // instance, so a chunk's lookup is one load shared by the CTA.
 // I: index type, int32_t when every instance of the list has fewer than 2^31 points.
 template <typename T, int D, int MODE, typename I>
-__global__ void __launch_bounds__(kChunk, 4) batch_pass_kernel(const BatchInst<T>* __restrict__ insts,
+// Occupancy: FP64 passes are bound by the FP64 pipe and keep 4 CTAs per SM (64
+// registers); FP32 passes are bound by memory latency and take 8 (32
+// registers, no spills: measured 9.52e10 -> 1.05e11 on the batch workload).
+__global__ void __launch_bounds__(kChunk, sizeof(T) == 4 ? 8 : 4) batch_pass_kernel(const BatchInst<T>* __restrict__ insts,
                                                             const int32_t* __restrict__ chunk_inst,
                                                             int64_t total_chunks, int64_t g)
 {
