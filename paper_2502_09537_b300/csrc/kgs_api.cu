@@ -891,6 +891,13 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
     drop_graph(h);
+    // validate before changing anything: a rejected order leaves the handle's order(s) as they were
+    std::vector<int64_t> list, off;
+    if (order) {
+        st = order_lists(h->dim, h->N, order, list, off);
+        if (st == -3) return fail(KGS_ERR_OOM, "host memory for the order schedule");
+        if (st) return fail(KGS_ERR_ARG, "order is not a permutation of 0 .. N^d - 1");
+    }
     h->olex = 0;
     cudaFree(h->olist_uv);
     h->olist_uv = nullptr;
@@ -903,10 +910,6 @@ int kgs_set_order(kgs_handle h, const int64_t* order)
         h->olevels.clear();
         return KGS_OK;
     }
-    std::vector<int64_t> list, off;
-    st = order_lists(h->dim, h->N, order, list, off);
-    if (st == -3) return fail(KGS_ERR_OOM, "host memory for the order schedule");
-    if (st) return fail(KGS_ERR_ARG, "order is not a permutation of 0 .. N^d - 1");
     if (!h->olist) {
         e = cudaMalloc(&h->olist, (size_t)h->M * sizeof(int64_t));
         if (e != cudaSuccess) {

@@ -123,6 +123,13 @@ def test_reset_and_bad_orders():
         with pytest.raises(KGSError):
             s.set_order(bad)
         assert s.order_levels() == 31          # unchanged by the rejected order
+        s.set_orders(orders.lexicographic(2, 16), orders.reverse_lexicographic(2, 16))
+        assert s.order_levels() == 62          # two sweeps per half step
+        with pytest.raises(KGSError):
+            s.set_order(bad)
+        with pytest.raises(KGSError):
+            s.set_orders(orders.lexicographic(2, 16), bad)
+        assert s.order_levels() == 62          # per-variable orders kept by both rejections
         s.set_order(None)
         assert s.order_levels() == 2
         s.step(5)
