@@ -140,13 +140,15 @@ def _worker(rank, world, port, prob, nsteps, out):
 
 
 @pytest.mark.parametrize("world", [1, 2, 3])
-@pytest.mark.parametrize("dim,N", [(2, 12), (3, 6)])
+@pytest.mark.parametrize("dim,N", [(2, 12), (3, 6), (2, 10)])
 def test_slabs_reproduce_the_whole_grid(orc, dim, N, world):
+    """(2, 10) on 3 ranks: slabs of 4, 3 and 3 planes, so the ranks' first
+    planes differ in parity and the colouring must come from global indices."""
     prob = Problem(dim, N, 7.0, 1.1, 0.9, 1.2, 0.8, 0.02)
     nsteps = 9
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 29600 + (os.getpid() + 17 * world + dim) % 900
+    port = 29600 + (os.getpid() + 17 * world + 5 * dim + N) % 900
     procs = [ctx.Process(target=_worker, args=(r, world, port, prob, nsteps, q)) for r in range(world)]
     for p in procs:
         p.start()
