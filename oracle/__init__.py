@@ -7,6 +7,7 @@ passages of the paper each function follows.
 """
 from .oracle import (  # noqa: F401
     MUT_ADJ_LITERAL, MUT_NO_REVERSE, MUT_RHO_OLD_BASE, MUT_ALPHA_2D, MUT_NO_ADJ_SWAP,
+    MUT_COLOUR_0BASED,
     checkerboard_order, steps_order, steps_orders2, steps_checkerboard, steps_checkerboard_omp,
     invariants, max_threads,
 )

@@ -59,6 +59,7 @@
 #define ORC_MUT_RHO_OLD_BASE  4  /* base (U,V) uses |Psi^n|^2 instead of |Psi^{n+1}|^2 */
 #define ORC_MUT_ALPHA_2D      8  /* Laplacian diagonal fixed at the 2D value 4 instead of 2d */
 #define ORC_MUT_NO_ADJ_SWAP  16  /* adjoint half keeps the base variable order (Psi, then U,V) */
+#define ORC_MUT_COLOUR_0BASED 32 /* colour rule on 0-based indices: red = 0-based index sum odd */
 
 typedef struct {
     int dim;
@@ -261,17 +262,23 @@ void orc_steps_orders2(int dim, int64_t N, double L, double kappa1, double kappa
     }
 }
 
-static int orc_is_red(const orc_ctx* c, int64_t i)
+/* Colour of point i (Sec. 4.2 figures; Algorithm 3's test on (j + k)): red
+ * when the sum of its 1-based indices is odd.  The planted mistake
+ * ORC_MUT_COLOUR_0BASED sums 0-based indices instead (the same colouring in
+ * 2D, the opposite one in 1D and 3D). */
+static int orc_is_red(const orc_ctx* c, int64_t i, int mut)
 {
     int64_t s = 0;
-    for (int a = 0; a < c->dim; ++a) s += (i / c->stride[a]) % c->N + 1;
+    int base = (mut & ORC_MUT_COLOUR_0BASED) ? 0 : 1;
+    for (int a = 0; a < c->dim; ++a) s += (i / c->stride[a]) % c->N + base;
     return (int)(s & 1);
 }
 
 /* Fill order[0..M) with the checkerboard order: the first colour's points in
  * lexicographic order, then the other colour's.  red_first = 1 gives the
- * paper's order (red first in the base half). */
-void orc_checkerboard_order(int dim, int64_t N, int red_first, int64_t* order)
+ * paper's order (red first in the base half); mut may plant
+ * ORC_MUT_COLOUR_0BASED. */
+void orc_checkerboard_order_mut(int dim, int64_t N, int red_first, int mut, int64_t* order)
 {
     orc_ctx c;
     orc_setup(&c, dim, N, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0);
@@ -279,8 +286,13 @@ void orc_checkerboard_order(int dim, int64_t N, int red_first, int64_t* order)
     for (int pass = 0; pass < 2; ++pass) {
         int want_red = (pass == 0) ? red_first : !red_first;
         for (int64_t i = 0; i < c.M; ++i)
-            if (orc_is_red(&c, i) == want_red) order[k++] = i;
+            if (orc_is_red(&c, i, mut) == want_red) order[k++] = i;
     }
+}
+
+void orc_checkerboard_order(int dim, int64_t N, int red_first, int64_t* order)
+{
+    orc_checkerboard_order_mut(dim, N, red_first, 0, order);
 }
 
 /* nsteps DP-AVF2 steps in the checkerboard order (red first), serial. */

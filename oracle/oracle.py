@@ -26,6 +26,7 @@ MUT_NO_REVERSE = 2
 MUT_RHO_OLD_BASE = 4
 MUT_ALPHA_2D = 8
 MUT_NO_ADJ_SWAP = 16
+MUT_COLOUR_0BASED = 32
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -53,6 +54,9 @@ def _load():
         lib.orc_steps_checkerboard_omp.restype = None
         lib.orc_checkerboard_order.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _i64p]
         lib.orc_checkerboard_order.restype = None
+        lib.orc_checkerboard_order_mut.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                                   ctypes.c_int, _i64p]
+        lib.orc_checkerboard_order_mut.restype = None
         lib.orc_invariants.argtypes = common + [_dp, _dp, _dp, _dp, _dp]
         lib.orc_invariants.restype = None
         lib.orc_max_threads.argtypes = []
@@ -73,10 +77,13 @@ def _check_state(dim, N, arrays):
             raise ValueError(f"oracle state must be C-contiguous float64 of shape {shape}")
 
 
-def checkerboard_order(dim: int, N: int, red_first: bool = True) -> np.ndarray:
+def checkerboard_order(dim: int, N: int, red_first: bool = True, mut: int = 0) -> np.ndarray:
+    """The checkerboard update order: one colour's points in lexicographic
+    order, then the other's; red first (the paper's order) unless red_first is
+    False.  mut may plant MUT_COLOUR_0BASED (tests of the colour pins)."""
     order = np.empty(N ** dim, dtype=np.int64)
-    _load().orc_checkerboard_order(dim, N, 1 if red_first else 0,
-                                   order.ctypes.data_as(_i64p))
+    _load().orc_checkerboard_order_mut(dim, N, 1 if red_first else 0, mut,
+                                       order.ctypes.data_as(_i64p))
     return order
 
 
