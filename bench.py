@@ -1,17 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the DP-AVF2 checkerboard solver (arXiv 2502.09537) on one B300.
 
-Workload (default): the 2D KGS problem on [-20,20)^2 with N = 2048^2 points,
-kappa1 = kappa2 = mu = gamma = 1, tau = 1e-3, 1000 DP-AVF2 steps in float64,
-psi0 = (1+i) exp(-r^2), u0 = exp(-r^2), v0 = 0 plus seeded Gaussian noise
-(sigma 1e-4); the discrete energy is evaluated every 100 steps.  One benchmark
-step = one such solve: load the initial state (already in HBM), 1000 steps,
-10 energy/mass evaluations.  Metric: grid-point updates per second
-(N^d x steps / time).  Multi-GPU: every rank solves its own instance (the
-instances are independent), value = all ranks' point-updates / max time.
+Workload (default): the 3D KGS problem on [-10,10)^3 with N = 512^3 points
+(134M points, 4.3 GB of float64 state), kappa1 = kappa2 = mu = gamma = 1,
+tau = 5e-4, 200 DP-AVF2 steps, psi0 = (1+i) exp(-|x|^2), u0 = exp(-|x|^2),
+v0 = 0 plus seeded Gaussian noise (sigma 1e-4); the discrete energy is
+evaluated every 100 steps.  One benchmark step = one such solve: load the
+initial state (already in HBM), 200 steps, 3 energy/mass evaluations.
+Metric: grid-point updates per second (N^d x steps / time).  `value` is the
+float64 solve; the line also carries the same workload with float32 state
+(its rate, roofline, speed-up, and its max-norm error and energy drift
+against the float64 run), the 96-instance batch in both precisions and a
+serving run at 50 requests/s (one timed step each).  Multi-GPU: every rank
+solves its own instance (the instances are independent), value = all ranks'
+point-updates / max time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload 2d|1d|3d] [--precision fp64|fp32]
+                    [--workload 3d|2d|1d|batch|serve] [--precision fp64|fp32]
 
 The reference arm (--impl reference) times the CPU oracle (oracle/, the
 OpenMP checkerboard twin, bitwise equal to the serial oracle) on the host's
@@ -67,20 +72,22 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
     return 3 * (2 * dim - 1) + 57.5
 
 
-# DRAM bytes per launch of the dominant kernel (a fused colour pass) from the
-# ncu captures summarised in profiles/ (dram__bytes_read.sum + write.sum), for
-# the kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 25.74e6,     # pass_kernel_fp64_kgs2d_N2048.md (RED_FUSED)
-               ("3d", "fp64"): 3.7645e9 + 2.1086e9,    # pass_kernel_fp64_kgs3d_N256.md (512^3 launch)
-               ("3d", "fp32"): 1.8822e9 + 1.0321e9}    # pass_kernel_fp32_kgs3d_N512.md (512^3 launch)
+# DRAM bytes per launch of the dominant kernel (a fused colour pass): the sum
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of that
+# launch on the workload's full grid (2D: a RED_FUSED pass of the 2048^2
+# grid; 3D: a pass launch of the 512^3 grid, one-pass metrics), for the
+# kernels as they are now; None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 25.74e6,
+               ("3d", "fp64"): 3.7645e9 + 2.1086e9,
+               ("3d", "fp32"): 1.8822e9 + 1.0321e9}
 
-def traffic_of(args):
+def traffic_of(args, precision=None):
     """DRAM bytes per pass launch from the ncu captures above: only for the
     launches they were taken on (the default one-per-pass kernel on the
     workload's full grid, checkerboard order); None otherwise."""
     if args.order != "checkerboard" or args.kernel not in (0, 1) or args.grid_n:
         return None
-    return NCU_TRAFFIC.get((args.workload, args.precision))
+    return NCU_TRAFFIC.get((args.workload, precision or args.precision))
 
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
@@ -222,25 +229,32 @@ def run_reference(args):
     }))
 
 
-def run_batch(args):
-    """The 96-instance batch: 64 2D grids N in {128..2048} and 32 3D grids N in
-    {64..256}, random parameters, tau = 5e-4, 500 steps, every instance in the
-    chosen precision, stepped by kgs_batch_step (one launch per colour pass over
-    all instances, replayed from a CUDA graph).  One benchmark step = load every
-    initial state from HBM, 500 steps."""
+def init_dist():
+    """(world, rank, local, dist module or None) from the torchrun environment;
+    sets the device and joins an NCCL group when there are several ranks."""
     import torch
-    from paper_2502_09537_b300 import build as kbuild
-    from paper_2502_09537_b300 import inputs
-    from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, Batch
-    kbuild.build()
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    precision = KGS_FP64 if args.precision == "fp64" else KGS_FP32
+    return world, rank, local, dist
+
+
+def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True):
+    """The 96-instance batch: 64 2D grids N in {128..2048} and 32 3D grids N in
+    {64..256}, random parameters, tau = 5e-4, 500 steps, every instance in the
+    chosen precision, stepped by kgs_batch_step (one launch per colour pass,
+    dimension and mode over all instances, replayed from a CUDA graph), with the
+    autotuner's persistent-CTA choice.  One benchmark step = load every initial
+    state from HBM, 500 steps.  Returns the measurement as a dict."""
+    import torch
+    from paper_2502_09537_b300 import inputs, tune
+    from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, Batch
+    precision = KGS_FP64 if precision_name == "fp64" else KGS_FP32
     elem = 8 if precision == KGS_FP64 else 4
     specs = inputs.batched_instances()
     nsteps = specs[0][1]
@@ -253,28 +267,29 @@ def run_batch(args):
     torch.cuda.synchronize()
     points = sum(p.points for p, _, _ in specs)
     stream = torch.cuda.Stream()
+    tuned_opts = tune.Tuner(tune.default_cache_path()).tune_batch_lists(
+        b, [(p, precision) for p, _, _ in specs], stream=stream) if tuned else {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one():
+    def load():
         for i, st in zip(ids, init):
             b.set_state(i, *st, stream=stream)
-        b.step(nsteps, stream=stream)
 
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            one()
+        for _ in range(warmup):
+            load()
+            b.step(nsteps, stream=stream)
         stream.synchronize()
         if dist:
             dist.barrier()
         times, kern = [], []
         l0 = b.launch_count
         with ClockSampler(local) as clk:
-            for _ in range(args.steps):
+            for _ in range(steps):
                 flush.zero_()
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record(stream)
-                for i, st in zip(ids, init):
-                    b.set_state(i, *st, stream=stream)
+                load()
                 e1.record(stream)
                 b.step(nsteps, stream=stream)
                 e2.record(stream)
@@ -284,10 +299,10 @@ def run_batch(args):
         launches = b.launch_count - l0
     from paper_2502_09537_b300.dist import max_over_ranks
     total_ms = max_over_ranks(sum(times), device="cuda")
-    value = world * points * nsteps * args.steps / (total_ms * 1e-3)
-    step_launches = 2 * nsteps + 1  # one pass launch per colour pass (one precision)
-    pass_ms = sum(kern) / (args.steps * step_launches)
-    upd_per_launch = points * nsteps / step_launches
+    value = world * points * nsteps * steps / (total_ms * 1e-3)
+    # the colour passes of one precision: a launch per pass, dimension and mode
+    pass_ms = sum(kern) / max(launches, 1)
+    upd_per_launch = points * nsteps * steps / max(launches, 1)
     peaks = measured_peaks()
     if precision == KGS_FP64:
         mean_dim_flops = sum(p.points * flops_per_point_update(p.dim) for p, _, _ in specs) / points
@@ -295,13 +310,13 @@ def run_batch(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
-                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and the red pass's V additions -- both in 1D/2D, one in 3D -- run on the integer pipes)"}
+                "work": "FP64-pipe flops of the colour passes"}
     else:
         achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6400.0),
                 "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6400.0), "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-    # end to end: host states in and out
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs of measured"}
+    # end to end: host states in and out (pinned), one solve
     host_in = [[torch.from_numpy(a.cpu().numpy()).pin_memory().numpy() for a in st] for st in init]
     host_out = [[np.empty_like(a) for a in st] for st in host_in]
     with torch.cuda.stream(stream):
@@ -313,70 +328,83 @@ def run_batch(args):
         for i, out in zip(ids, host_out):
             b.get_state(i, out, stream=stream)
         e2e_s = time.perf_counter() - t0
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
-        "data": "synthetic",
+    b.close()
+    return {
+        "value": value, "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+        "dtype": "f64" if elem == 8 else "f32",
         "config": {"workload": "kgs_batch96", "instances": len(specs), "points": points,
-                   "steps_per_solve": nsteps, "precision": args.precision,
-                   "l2": "256 MB buffer written between timed steps",
-                   "parallelism": f"{world} independent batch(es), one per GPU"},
+                   "steps_per_solve": nsteps, "precision": precision_name,
+                   "tuned": tuned_opts,
+                   "l2": "256 MB buffer written between timed steps"},
         "roofline": roof,
         "e2e": {"value": world * points * nsteps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": points * 32, "d2h_bytes_per_step": points * 32},
-        "gpu_launches": launches, "clocks": clk.summary(),
-        "kernel_ms_per_launch": pass_ms,
+        "gpu_launches": launches, "clocks": clk.summary(), "kernel_ms_per_launch": pass_ms,
     }
-    b.close()
+
+
+def run_batch(args):
+    world, rank, local, dist = init_dist()
+    from paper_2502_09537_b300 import build as kbuild
+    kbuild.build()
+    leg = batch_leg(args.precision, args.steps, args.warmup, world, local, dist, tuned=not args.untuned)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    line.update(leg)
+    line["config"]["parallelism"] = f"{world} independent batch(es), one per GPU"
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-    if int(os.environ.get("RANK", "0")) == 0:
+    if rank == 0:
         print(json.dumps(line))
 
 
-def run_serve(args):
+def serve_leg(rate, requests, steps, warmup, max_steps, turn_work, world, rank, local, tuned=True):
     """Continuous-batching serving: Poisson arrivals of solve requests (dim in
     {1,2,3}, N in [256,8192] / [128,2048]^2 / [64,384]^3, steps uniform in
-    [100, --max-steps], FP32 or FP64 each, parameters as the batched workload),
+    [100, max_steps], FP32 or FP64 each, parameters as the batched workload),
     admitted by a 150 GB device-memory budget, states resident on the device.
-    One benchmark step = serving --requests requests from their arrival to
+    One benchmark step = serving `requests` requests from their arrival to
     their result on the host; value = point-updates/s over the step, with
     p50/p99 request latency and the worst per-request energy drift."""
     import torch
-    from paper_2502_09537_b300 import build as kbuild
     from paper_2502_09537_b300 import serve
-    kbuild.build()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     budget = 150 * (1 << 30)
     stream = torch.cuda.Stream()
+    batch_options, chosen = {}, {}
+    if tuned:
+        # the autotuner's per-list launch shapes, timed on a mix drawn from the
+        # request distribution (capped at 8 GB of state)
+        from paper_2502_09537_b300 import tune
+        mix, used = [], 0
+        for r in serve.poisson_requests(rate, 32, seed=SEED_SERVE - 1, step_range=(100, max_steps)):
+            nb = serve.state_bytes(r.prob, r.precision)
+            if used + nb <= (8 << 30):
+                mix.append((r.prob, r.precision))
+                used += nb
+        batch_options = serve.tuned_batch_options(tune.Tuner(tune.default_cache_path()), mix, stream=stream)
+        chosen = {tune.list_name_of_option(k): v for k, v in batch_options.items()}
     lat, pts, wall, drift_max, turns = [], 0, 0.0, 0.0, 0
+    service = []
     launches = 0
     with torch.cuda.stream(stream):
         with ClockSampler(local) as clk:
-            for k in range(args.warmup + args.steps):
-                reqs = serve.poisson_requests(args.rate, args.requests, seed=SEED_SERVE + 1000 * rank + k,
-                                              step_range=(100, args.max_steps))
+            for k in range(warmup + steps):
+                reqs = serve.poisson_requests(rate, requests, seed=SEED_SERVE + 1000 * rank + k,
+                                              step_range=(100, max_steps))
                 srv = serve.Server(budget, quantum=100, stream=stream, keep_state=True,
-                                   turn_work=args.turn_work)
+                                   turn_work=turn_work, batch_options=batch_options)
                 for r in reqs:
                     srv.submit(r)
                 l0 = srv.batch.launch_count
                 t0 = time.perf_counter()
                 res = srv.run()
                 dt = time.perf_counter() - t0
-                if k >= args.warmup:
+                if k >= warmup:
                     wall += dt
                     pts += srv.point_updates
                     lat += [r.latency for r in res]
+                    service += [r.finished - r.admitted for r in res]
                     drift_max = max(drift_max, max(r.energy_drift for r in res))
                     turns += srv.turns
                     launches += srv.batch.launch_count - l0
@@ -384,16 +412,16 @@ def run_serve(args):
     from paper_2502_09537_b300.dist import max_over_ranks
     wall = max_over_ranks(wall, device="cuda")
     value = world * pts / wall
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "kgs_serve", "rate_per_s": args.rate,
-                   "requests_per_step": args.requests, "step_range": [100, args.max_steps],
-                   "budget_bytes": budget, "quantum_steps": 100, "turn_work": args.turn_work,
-                   "l2": "inputs are built per request on the host (cold)",
-                   "parallelism": f"{world} independent server(s), one per GPU"},
+    return {
+        "value": value, "ms_per_step": 1e3 * wall / steps, "steps": steps, "warmup": warmup,
+        "dtype": "f64+f32",
+        "config": {"workload": "kgs_serve", "rate_per_s": rate,
+                   "requests_per_step": requests, "step_range": [100, max_steps],
+                   "budget_bytes": budget, "quantum_steps": 100, "turn_work": turn_work,
+                   "tuned_batch_options": chosen,
+                   "l2": "inputs are built per request on the host (cold)"},
         "latency_s": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99)},
+        "residence_s": {"p50": serve.percentile(service, 50), "p99": serve.percentile(service, 99)},
         "requests_per_s": world * len(lat) / wall,
         "energy_drift_max": drift_max,
         "e2e": {"value": value, "unit": UNIT,
@@ -401,11 +429,25 @@ def run_serve(args):
                         "inside the timed region"},
         "gpu_launches": launches, "clocks": clk.summary(), "turns": turns,
     }
+
+
+def run_serve(args):
+    world, rank, local, dist = init_dist()
+    from paper_2502_09537_b300 import build as kbuild
+    kbuild.build()
+    rates = [float(r) for r in str(args.rate).split(",")]
+    for rate in rates:
+        leg = serve_leg(rate, args.requests, args.steps, args.warmup, args.max_steps, args.turn_work,
+                        world, rank, local)
+        line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+        line.update(leg)
+        line["config"]["parallelism"] = f"{world} independent server(s), one per GPU"
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(line))
 
 
 SEED_SERVE = 2502_09537 + 4
@@ -435,25 +477,170 @@ def solve(s, stream, init, nsteps, per_chunk_events=None, step_launches=None):
     return seen
 
 
+def configure(s, args, prob):
+    """Apply the command line's kernel options and update order to a solver."""
+    from paper_2502_09537_b300 import solver as ks
+    for flag, opt in ((args.threads, ks.KGS_OPT_THREADS), (args.kernel, ks.KGS_OPT_KERNEL),
+                      (args.ppt, ks.KGS_OPT_PPT), (args.slab_planes, ks.KGS_OPT_SLAB_PLANES),
+                      (args.wave_lag, ks.KGS_OPT_WAVE_LAG), (args.wave_chunk, ks.KGS_OPT_WAVE_CHUNK),
+                      (args.order_mode, ks.KGS_OPT_ORDER_MODE)):
+        if flag:
+            s.set_option(opt, flag)
+    if args.pdl >= 0:
+        s.set_option(ks.KGS_OPT_PDL, args.pdl)
+    if args.order == "lex-rev":
+        from paper_2502_09537_b300 import orders
+        s.set_orders(orders.lexicographic(prob.dim, prob.N), orders.reverse_lexicographic(prob.dim, prob.N))
+    elif args.order != "checkerboard":
+        from paper_2502_09537_b300 import orders
+        s.set_order(orders.lexicographic(prob.dim, prob.N) if args.order == "lex"
+                    else orders.block_split_2d(prob.N, 16))
+
+
+def solo_leg(args, work, precision_name, init_dev, flush, local, dist, world, steps, warmup):
+    """Time `steps` solves of the workload (after `warmup` untimed ones) in one
+    precision, CUDA events on the solver's stream; returns the measurement and
+    the solver (open, holding the last solve's final state)."""
+    import torch
+    from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, Solver, probe_fma_rate
+    prob = work.prob
+    precision = KGS_FP64 if precision_name == "fp64" else KGS_FP32
+    elem = 8 if precision == KGS_FP64 else 4
+    stream = torch.cuda.Stream()
+    nchunks = (work.nsteps + ENERGY_EVERY - 1) // ENERGY_EVERY
+    s = Solver.from_problem(prob, precision)
+    configure(s, args, prob)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            solve(s, stream, init_dev, work.nsteps)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        iter_ms, kern_ms = [], []
+        step_launches = [0]
+        launches0 = s.launch_count
+        drift = 0.0
+        with ClockSampler(local) as clk:
+            for _ in range(steps):
+                flush.zero_()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(nchunks)]
+                kev = list(ev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                seen = solve(s, stream, init_dev, work.nsteps, per_chunk_events=kev,
+                             step_launches=step_launches)
+                e1.record(stream)
+                stream.synchronize()
+                iter_ms.append(e0.elapsed_time(e1))
+                kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+                E0, S0, _ = seen[0]
+                drift = max(drift, max(abs(E - E0) / max(S0, S) for E, S, _ in seen))
+        launches = s.launch_count - launches0
+    from paper_2502_09537_b300.dist import max_over_ranks
+    total_ms = max_over_ranks(sum(iter_ms), device="cuda")
+    pts_per_step = prob.points * work.nsteps
+    value = world * pts_per_step * steps / (total_ms * 1e-3)
+    # roofline of the dominant kernel (the colour-pass kernels that run inside
+    # kgs_step): algorithmic work per launch / average launch duration, both
+    # over the timed region
+    pass_ms = sum(kern_ms) / step_launches[0]
+    upd_per_launch = pts_per_step * steps / step_launches[0]
+    peaks = measured_peaks()
+    if precision == KGS_FP64:
+        fma_rate, _ = probe_fma_rate(64, 2048, 8, stream)
+        fpu = (flops_per_point_update(prob.dim) if args.order == "checkerboard"
+               else flops_per_point_update_unfused(prob.dim))
+        achieved = upd_per_launch * fpu / (pass_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": traffic_of(args, precision_name),
+                "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
+                "probe_tflops": 2 * fma_rate / 1e12,
+                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and the red pass's V additions -- both in 1D/2D, one in 3D -- run on the integer pipes)",
+                "flops_per_point_update": fpu,
+                "algorithmic_flops_per_point_update": algorithmic_flops_per_point_update(prob.dim),
+                "algorithmic_tflops": upd_per_launch * algorithmic_flops_per_point_update(prob.dim)
+                / (pass_ms * 1e-3) / 1e12,
+                "hbm_frac": bytes_per_point_update(elem) * upd_per_launch / (pass_ms * 1e-3)
+                / 1e9 / peaks.get("hbm_gbs", 6400.0)}
+    else:
+        achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6400.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": traffic_of(args, precision_name),
+                "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                                else "fallback 6.4 TB/s (of fallback)"),
+                "bytes_per_point_update": bytes_per_point_update(elem)}
+    leg = {
+        "value": value, "ms_per_step": total_ms / steps,
+        "ms_per_step_median": float(np.median(iter_ms)), "steps": steps, "warmup": warmup,
+        "dtype": "f64" if elem == 8 else "f32", "roofline": roof, "gpu_launches": launches,
+        "clocks": clk.summary(), "energy_drift": drift, "kernel_ms_per_launch": pass_ms,
+        "kernel_launches_per_solve": step_launches[0] / steps,
+    }
+    return leg, s, stream
+
+
+def e2e_leg(s, stream, work, flush, world, steps):
+    """The same solve end to end through the C ABI with host buffers: pinned
+    initial state in, final state out, both copies inside the timed region."""
+    import torch
+    prob = work.prob
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in work.state]
+    host_out = [torch.empty(a.shape, dtype=torch.float64).pin_memory().numpy() for a in work.state]
+    with torch.cuda.stream(stream):
+        e2e_ms = []
+        for _ in range(max(1, min(steps, 3))):
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            solve(s, stream, host_in, work.nsteps)
+            s.get_state(host_out, stream=stream)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    del host_in, host_out
+    return {"value": world * prob.points * work.nsteps * len(e2e_ms) / (sum(e2e_ms) * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": 4 * prob.points * 8, "d2h_bytes_per_step": 4 * prob.points * 8}
+
+
+def final_state_dev(s, prob):
+    import torch
+    out = tuple(torch.empty((prob.N,) * prob.dim, dtype=torch.float64, device="cuda") for _ in range(4))
+    s.get_state(out)
+    torch.cuda.synchronize()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "1d", "3d", "batch", "serve"])
-    ap.add_argument("--rate", type=float, default=50.0, help="serving: request arrival rate (1/s)")
+    ap.add_argument("--workload", default="3d", choices=["3d", "2d", "1d", "batch", "serve"],
+                    help="3d (default): the 512^3 configuration in FP64 with an FP32 leg; 2d: "
+                         "2048^2; 1d: the 512-point soliton; batch: the 96 instances; serve: "
+                         "continuous batching")
+    ap.add_argument("--rate", default="50", help="serving: request arrival rate(s) (1/s), comma-separated")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests per timed step")
     ap.add_argument("--turn-work", type=float, default=5e9,
                     help="serving: point-updates per turn, shortest remaining work first (0: all)")
-    ap.add_argument("--max-steps", type=int, default=1000,
-                    help="serving: upper end of the per-request step range (workload: 10000)")
+    ap.add_argument("--max-steps", type=int, default=10000,
+                    help="serving: upper end of the per-request step range (the workload's 10000)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="3d: skip the FP32 leg")
+    ap.add_argument("--no-summaries", action="store_true",
+                    help="3d: skip the compact batch and serve summaries")
+    ap.add_argument("--untuned", action="store_true", help="batch: library defaults, no autotuner")
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent, "
-                         "5 slab-pipelined passes, 6 wave (a step's two passes in one launch)")
+                         "5 slab-pipelined passes, 6 wave (a step's two passes in one launch), "
+                         "7 streamed planes (3D FP32: a step's two passes per axis-0 plane, TMA-staged)")
     ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab and wave kernels)")
     ap.add_argument("--wave-lag", type=int, default=0, help="KGS_OPT_WAVE_LAG (wave kernel)")
     ap.add_argument("--wave-chunk", type=int, default=0, help="KGS_OPT_WAVE_CHUNK (wave kernel)")
@@ -485,146 +672,24 @@ def main():
 
     import torch
     from paper_2502_09537_b300 import build as kbuild
-    from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, Solver, probe_fma_rate
     kbuild.build()
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    world, rank, local, dist = init_dist()
 
     work = make_workload(args.workload, args.grid_n)
     if args.steps_per_solve:
         work = work._replace(nsteps=args.steps_per_solve)
     prob = work.prob
-    precision = KGS_FP64 if args.precision == "fp64" else KGS_FP32
-    elem = 8 if precision == KGS_FP64 else 4
-    stream = torch.cuda.Stream()
     init_dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in work.state]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    nchunks = (work.nsteps + ENERGY_EVERY - 1) // ENERGY_EVERY
-    s = Solver.from_problem(prob, precision)
-    from paper_2502_09537_b300.solver import KGS_OPT_PPT, KGS_OPT_THREADS
-    if args.threads:
-        s.set_option(KGS_OPT_THREADS, args.threads)
-    if args.kernel:
-        from paper_2502_09537_b300.solver import KGS_OPT_KERNEL
-        s.set_option(KGS_OPT_KERNEL, args.kernel)
-    if args.ppt:
-        s.set_option(KGS_OPT_PPT, args.ppt)
-    if args.slab_planes:
-        from paper_2502_09537_b300.solver import KGS_OPT_SLAB_PLANES
-        s.set_option(KGS_OPT_SLAB_PLANES, args.slab_planes)
-    if args.wave_lag:
-        from paper_2502_09537_b300.solver import KGS_OPT_WAVE_LAG
-        s.set_option(KGS_OPT_WAVE_LAG, args.wave_lag)
-    if args.wave_chunk:
-        from paper_2502_09537_b300.solver import KGS_OPT_WAVE_CHUNK
-        s.set_option(KGS_OPT_WAVE_CHUNK, args.wave_chunk)
-    if args.pdl >= 0:
-        from paper_2502_09537_b300.solver import KGS_OPT_PDL
-        s.set_option(KGS_OPT_PDL, args.pdl)
-    if args.order_mode:
-        from paper_2502_09537_b300.solver import KGS_OPT_ORDER_MODE
-        s.set_option(KGS_OPT_ORDER_MODE, args.order_mode)
-    if args.order == "lex-rev":
-        from paper_2502_09537_b300 import orders
-        s.set_orders(orders.lexicographic(prob.dim, prob.N), orders.reverse_lexicographic(prob.dim, prob.N))
-    elif args.order != "checkerboard":
-        from paper_2502_09537_b300 import orders
-        s.set_order(orders.lexicographic(prob.dim, prob.N) if args.order == "lex"
-                    else orders.block_split_2d(prob.N, 16))
-    torch.cuda.synchronize()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            solve(s, stream, init_dev, work.nsteps)
-        stream.synchronize()
-        if dist:
-            dist.barrier()
-        iter_ms, kern_ms = [], []
-        step_launches = [0]
-        launches0 = s.launch_count
-        drift = 0.0
-        with ClockSampler(local) as clk:
-            for _ in range(args.steps):
-                flush.zero_()
-                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                      for _ in range(nchunks)]
-                kev = list(ev)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                seen = solve(s, stream, init_dev, work.nsteps, per_chunk_events=kev,
-                             step_launches=step_launches)
-                e1.record(stream)
-                stream.synchronize()
-                iter_ms.append(e0.elapsed_time(e1))
-                kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
-                E0, S0, _ = seen[0]
-                drift = max(drift, max(abs(E - E0) / max(S0, S) for E, S, _ in seen))
-        launches = s.launch_count - launches0
-    from paper_2502_09537_b300.dist import max_over_ranks
-    total_ms = max_over_ranks(sum(iter_ms), device="cuda")
-    pts_per_step = prob.points * work.nsteps
-    value = world * pts_per_step * args.steps / (total_ms * 1e-3)
-
-    # end to end through the C ABI with host buffers (pinned)
-    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in work.state]
-    host_out = [torch.empty(a.shape, dtype=torch.float64).pin_memory().numpy() for a in work.state]
-    with torch.cuda.stream(stream):
-        e2e_ms = []
-        for _ in range(max(1, min(args.steps, 3))):
-            flush.zero_()
-            stream.synchronize()
-            t0 = time.perf_counter()
-            solve(s, stream, host_in, work.nsteps)
-            s.get_state(host_out, stream=stream)
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = world * pts_per_step * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
-
-    # roofline of the dominant kernel (the colour-pass / tile kernel that runs
-    # inside kgs_step): algorithmic work per launch / average launch duration,
-    # both over the timed region
-    pass_ms = sum(kern_ms) / step_launches[0]
-    upd_per_launch = prob.points * work.nsteps * args.steps / step_launches[0]
-    peaks = measured_peaks()
-    if precision == KGS_FP64:
-        fma_rate, _ = probe_fma_rate(64, 2048, 8, stream)
-        fpu = (flops_per_point_update(prob.dim) if args.order == "checkerboard"
-               else flops_per_point_update_unfused(prob.dim))
-        flops_per_launch = upd_per_launch * fpu
-        achieved = flops_per_launch / (pass_ms * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": traffic_of(args),
-                "peak_source": "derived: 148 SMs x 2 FP64 FMA/cycle x 2 flops x 2032 MHz",
-                "probe_tflops": 2 * fma_rate / 1e12,
-                "work": "FP64-pipe flops (neighbour sums, beta S, B'S_U, 2r, 1/(1+r^2) and the red pass's V additions -- both in 1D/2D, one in 3D -- run on the integer pipes)",
-                "flops_per_point_update": fpu,
-                "algorithmic_flops_per_point_update": algorithmic_flops_per_point_update(prob.dim),
-                "algorithmic_tflops": upd_per_launch * algorithmic_flops_per_point_update(prob.dim)
-                / (pass_ms * 1e-3) / 1e12,
-                "hbm_frac": bytes_per_point_update(elem) * upd_per_launch / (pass_ms * 1e-3)
-                / 1e9 / peaks.get("hbm_gbs", 6400.0)}
-    else:
-        bytes_per_launch = upd_per_launch * bytes_per_point_update(elem)
-        achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
-        peak = peaks.get("hbm_gbs", 6400.0)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak,
-                "traffic": traffic_of(args),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
-
+    leg, s, stream = solo_leg(args, work, args.precision, init_dev, flush, local, dist, world,
+                              args.steps, args.warmup)
+    e2e = e2e_leg(s, stream, work, flush, world, args.steps)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "ms_per_step_median": float(np.median(iter_ms)), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32",
+        "metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": leg["ms_per_step"],
+        "ms_per_step_median": leg["ms_per_step_median"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": leg["dtype"],
         "data": "synthetic",
         "config": {"workload": work.name, "dim": prob.dim, "N": prob.N, "L": prob.L,
                    "threads": args.threads or 256, "kernel": args.kernel, "order": args.order,
@@ -635,18 +700,63 @@ def main():
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
-        "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": 4 * prob.points * 8, "d2h_bytes_per_step": 4 * prob.points * 8},
-        "gpu_launches": launches,
-        "clocks": clk.summary(),
-        "energy_drift": drift,
-        "kernel_ms_per_launch": pass_ms,
-        "kernel_launches_per_solve": step_launches[0] / args.steps,
+        "roofline": leg["roofline"],
+        "e2e": e2e,
+        "gpu_launches": leg["gpu_launches"],
+        "clocks": leg["clocks"],
+        "energy_drift": leg["energy_drift"],
+        "kernel_ms_per_launch": leg["kernel_ms_per_launch"],
+        "kernel_launches_per_solve": leg["kernel_launches_per_solve"],
     }
+
+    # FP32 state against FP64 on the same workload: its own timing and
+    # roofline, the speed-up, and its max-norm error and energy drift against
+    # the FP64 run (the FP64 path equals the FP64 oracle to 1e-12, tested)
+    if args.precision == "fp64" and not args.no_fp32 and args.workload in ("3d", "2d"):
+        ref = final_state_dev(s, prob)
+        s.close()
+        leg32, s32, _ = solo_leg(args, work, "fp32", init_dev, flush, local, dist, world,
+                                 args.steps, min(args.warmup, 3))
+        got = final_state_dev(s32, prob)
+        s32.close()
+        errs = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(got, ref)]
+        del got, ref
+        line["fp32"] = {
+            "value": leg32["value"], "unit": UNIT, "ms_per_step": leg32["ms_per_step"],
+            "speedup_vs_fp64": leg32["value"] / leg["value"],
+            "max_norm_rel_err_vs_fp64": max(errs),
+            "max_norm_rel_err_per_field": dict(zip(("P", "Q", "U", "V"), errs)),
+            "energy_drift": leg32["energy_drift"], "roofline": leg32["roofline"],
+            "gpu_launches": leg32["gpu_launches"], "clocks": leg32["clocks"],
+            "kernel_ms_per_launch": leg32["kernel_ms_per_launch"],
+            "kernel_launches_per_solve": leg32["kernel_launches_per_solve"],
+            "note": "error of the FP32-state run against the FP64 run from the same initial state, "
+                    "per field max|x32 - x64| / max|x64| after the whole solve",
+        }
+        line["gpu_launches"] += leg32["gpu_launches"]
+    else:
+        s.close()
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline: N = 1 only
         line["cpu_baseline"] = cpu_baseline(work)
-    s.close()
+    del init_dev
+    torch.cuda.empty_cache()
+
+    # compact summaries of the batched and served workloads (one timed step each)
+    if args.workload == "3d" and not args.no_summaries and not args.grid_n:
+        summ = {}
+        for name in ("fp64", "fp32"):
+            b = batch_leg(name, 1, 1, world, local, dist)
+            summ[name] = {k: b[k] for k in ("value", "ms_per_step", "roofline", "gpu_launches",
+                                            "kernel_ms_per_launch")}
+            summ[name]["tuned"] = b["config"]["tuned"]
+        summ["config"] = {"workload": "kgs_batch96", "instances": 96, "steps_per_solve": 500,
+                          "timed_steps": 1, "warmup": 1}
+        line["batch"] = summ
+        sv = serve_leg(50.0, 16, 1, 0, 10000, args.turn_work, world, rank, local)
+        line["serve"] = {k: sv[k] for k in ("value", "latency_s", "residence_s", "requests_per_s",
+                                            "energy_drift_max", "gpu_launches", "turns")}
+        line["serve"]["config"] = sv["config"]
     if dist:
         dist.barrier()
         dist.destroy_process_group()

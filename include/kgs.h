@@ -279,8 +279,13 @@ int kgs_last_status(void);
  * fit and their space is returned by kgs_batch_remove. */
 typedef struct kgs_batch* kgs_batch_handle;
 
-#define KGS_BATCH_OPT_CTAS_PER_SM 1  /* persistent CTAs per SM, 1..32 (default 8) */
+#define KGS_BATCH_OPT_CTAS_PER_SM 1  /* persistent CTAs per SM, 1..32 (default 8), every list */
 #define KGS_BATCH_OPT_GRAPH       2  /* 0 off, 1 capture step calls in a CUDA graph (default 1) */
+/* Persistent CTAs per SM of one list of instances -- one precision and
+ * dimension, whose passes share a launch: option KGS_BATCH_OPT_CTAS_LIST +
+ * 3 p + (dim - 1), p = 0 for FP64 and 1 for FP32, value 1..32, or 0 to follow
+ * KGS_BATCH_OPT_CTAS_PER_SM again (which also resets every list). */
+#define KGS_BATCH_OPT_CTAS_LIST   16
 
 /* Create a batch on `device` (-1 = current) with an arena of capacity_bytes
  * (>= 4096).  NULL on error (kgs_last_status / kgs_last_error). */

@@ -196,6 +196,7 @@ struct kgs_batch {
     int64_t graph_launches = 0;  // kernels per replay of the graph
     // stepping
     int ctas_per_sm = 8;
+    int ctas_list[2][3] = {{0, 0, 0}, {0, 0, 0}};  // per (precision, dimension); 0 = ctas_per_sm
     int use_graph = 1;
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;  // step counts the graph was captured for
@@ -408,7 +409,8 @@ int launch_one(kgs_batch* b, const kgs_batch::DevList& dl, int64_t chunks, bool 
 {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    const int64_t grid = std::min<int64_t>(chunks, (int64_t)sms * b->ctas_per_sm);
+    const int lc = b->ctas_list[sizeof(T) == 8 ? 0 : 1][D - 1];
+    const int64_t grid = std::min<int64_t>(chunks, (int64_t)sms * (lc > 0 ? lc : b->ctas_per_sm));
     const BatchInst<T>* insts = reinterpret_cast<const BatchInst<T>*>(dl.inst);
     if (wide)
         batch_pass_kernel<T, D, MODE, int64_t><<<(unsigned)grid, kChunk, 0, s>>>(insts, dl.chunk_inst, chunks, g);
@@ -830,8 +832,22 @@ int kgs_batch_set_option(kgs_batch_handle b, int option, int64_t value)
     case KGS_BATCH_OPT_CTAS_PER_SM:
         if (value < 1 || value > 32) return bfail(KGS_ERR_ARG, "CTAs per SM take 1..32");
         b->ctas_per_sm = (int)value;
+        for (auto& row : b->ctas_list)
+            for (int& c : row) c = 0;
         drop_batch_graph(b);
         return KGS_OK;
+    case KGS_BATCH_OPT_CTAS_LIST + 0:
+    case KGS_BATCH_OPT_CTAS_LIST + 1:
+    case KGS_BATCH_OPT_CTAS_LIST + 2:
+    case KGS_BATCH_OPT_CTAS_LIST + 3:
+    case KGS_BATCH_OPT_CTAS_LIST + 4:
+    case KGS_BATCH_OPT_CTAS_LIST + 5: {
+        if (value < 0 || value > 32) return bfail(KGS_ERR_ARG, "CTAs per SM of a list take 0..32");
+        const int k = option - KGS_BATCH_OPT_CTAS_LIST;
+        b->ctas_list[k / 3][k % 3] = (int)value;
+        drop_batch_graph(b);
+        return KGS_OK;
+    }
     case KGS_BATCH_OPT_GRAPH:
         if (value < 0 || value > 1) return bfail(KGS_ERR_ARG, "graph option takes 0 or 1");
         b->use_graph = (int)value;

@@ -87,8 +87,13 @@ class Server:
     def __init__(self, budget_bytes: int, quantum: int = 100, max_slots: int = 256,
                  device: int = -1, clock: Callable[[], float] = time.perf_counter,
                  stream=None, keep_state: bool = True, prepare_ahead: int = 8,
-                 turn_work: float = 0.0, max_wait: float = 5.0):
+                 turn_work: float = 0.0, max_wait: float = 5.0,
+                 batch_options: Optional[Dict[int, int]] = None):
         self.batch = Batch(budget_bytes, device)
+        # launch shapes (kgs_batch_set_option), e.g. the autotuner's per-list
+        # persistent CTAs from tuned_batch_options
+        for k, v in (batch_options or {}).items():
+            self.batch.set_option(k, v)
         self.budget = budget_bytes
         self.quantum = quantum
         # shortest-remaining-work-first turns: point-updates per turn (0: advance
@@ -195,6 +200,31 @@ class Server:
             if not until_empty:
                 break
         return self.results
+
+
+def tuned_batch_options(tuner, members, nsteps: int = 8, stream=None, device: int = -1) -> Dict[int, int]:
+    """Per-list persistent CTAs per SM for serving a mix like `members` (a
+    list of (problem, precision)): the tuner times them on a batch of those
+    problems holding zero states (timing does not depend on the values), and
+    the choice is returned as batch options for Server(batch_options=...)."""
+    import torch
+    from . import tune
+    need = sum(state_bytes(p, prec) + 512 for p, prec in members)
+    b = Batch(need + (16 << 20), device)
+    try:
+        for p, prec in members:
+            i = b.add(p, prec)
+            z = torch.zeros((p.N,) * p.dim, dtype=torch.float64, device="cuda")
+            b.set_state(i, z, z, z, z, stream=stream)
+        chosen = tuner.tune_batch_lists(b, members, nsteps=nsteps, stream=stream)
+    finally:
+        b.close()
+    opts = {}
+    for p, prec in members:
+        name = tune.list_name(prec, p.dim)
+        if name in chosen:
+            opts[tune.list_option(prec, p.dim)] = chosen[name]
+    return opts
 
 
 def select_turn(items, quantum: int, turn_work: float, max_wait: float, now: float) -> List[int]:

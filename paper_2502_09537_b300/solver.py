@@ -318,6 +318,7 @@ def probe_psi_weight(r, stream=None):
 
 KGS_BATCH_OPT_CTAS_PER_SM = 1
 KGS_BATCH_OPT_GRAPH = 2
+KGS_BATCH_OPT_CTAS_LIST = 16  # + 3 p + (dim - 1), p = 0 FP64 / 1 FP32
 
 
 class Batch:

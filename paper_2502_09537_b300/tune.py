@@ -11,7 +11,10 @@ problem of that bucket and keeps the fastest:
     passes per launch, threads per CTA) that fit in shared memory;
   * the shared-memory resident kernel, when the grid fits in one CTA.
 
-For a batch it chooses the number of persistent CTAs per SM.  Every option
+For a batch it chooses the number of persistent CTAs per SM, for the whole
+batch or per list of instances (one precision and dimension: the instances
+whose colour passes share a launch), by coordinate descent over the lists
+with the whole batch's step timed.  Every option
 computes bitwise the same state (the kernels share their pointwise code), so
 tuning changes only speed.  Timing uses CUDA events around kgs_step on the
 caller's stream after warm-up steps; a timer can be injected (the CPU tests
@@ -24,7 +27,7 @@ import math
 import os
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
-from .solver import (KGS_BATCH_OPT_CTAS_PER_SM, KGS_FP64, KGS_OPT_KERNEL, KGS_OPT_THREADS,
+from .solver import (KGS_BATCH_OPT_CTAS_LIST, KGS_BATCH_OPT_CTAS_PER_SM, KGS_FP64, KGS_OPT_KERNEL, KGS_OPT_THREADS,
                      KGS_OPT_TILE_LX, KGS_OPT_TILE_PASSES, KGS_OPT_TILE_T1, KGS_OPT_TILE_T2,
                      KGS_OPT_TILE_THREADS)
 
@@ -68,6 +71,26 @@ def candidates(prob, precision: int) -> List[Options]:
                 o[KGS_OPT_TILE_T1] = T1
             out.append(o)
     return out
+
+
+def list_option(precision: int, dim: int) -> int:
+    """The batch option that sets one list's persistent CTAs per SM."""
+    return KGS_BATCH_OPT_CTAS_LIST + 3 * (0 if precision == KGS_FP64 else 1) + dim - 1
+
+
+def list_name(precision: int, dim: int) -> str:
+    return "%s_%dd" % ("fp64" if precision == KGS_FP64 else "fp32", dim)
+
+
+def list_name_of_option(option: int) -> str:
+    """The list name of a KGS_BATCH_OPT_CTAS_LIST option."""
+    k = option - KGS_BATCH_OPT_CTAS_LIST
+    return list_name(KGS_FP64 if k < 3 else 0, k % 3 + 1)
+
+
+def default_cache_path() -> Optional[str]:
+    """The JSON cache named by KGS_TUNE_CACHE, or None (in-memory only)."""
+    return os.environ.get("KGS_TUNE_CACHE") or None
 
 
 def apply(solver, options: Options) -> None:
@@ -160,3 +183,45 @@ class Tuner:
                 best, best_ms = c, ms
         batch.set_option(KGS_BATCH_OPT_CTAS_PER_SM, best)
         return best
+
+    def tune_batch_lists(self, batch, members: Sequence[Tuple[object, int]], nsteps: int = 8,
+                         values: Sequence[int] = (2, 4, 8, 16), warmup: int = 1,
+                         timer: Optional[Callable] = None, stream=None) -> Dict[str, int]:
+        """Persistent CTAs per SM of every list of a batch (members: the
+        (problem, precision) of its live instances).  Lists are tuned one at a
+        time, the others held at their current choice, each value timed over
+        batch.step(nsteps) after `warmup` untimed calls (a changed option makes
+        the next call capture a new graph).  The choice is set on the batch,
+        cached per (list, total points rounded up to a power of two) and
+        returned as {list name: CTAs per SM}."""
+        t = timer or (lambda b, n: self.timer(b, n, stream) if self.timer is cuda_event_timer
+                      else self.timer(b, n))
+        points: Dict[Tuple[int, int], int] = {}
+        for prob, prec in members:
+            k = (prec, prob.dim)
+            points[k] = points.get(k, 0) + prob.points
+        chosen: Dict[str, int] = {}
+        todo = []
+        for (prec, dim), pts in sorted(points.items()):
+            key = "batch:%s:%d" % (list_name(prec, dim), 1 << max(0, math.ceil(math.log2(pts))))
+            if key in self.cache:
+                v = int(self.cache[key][0])
+                batch.set_option(list_option(prec, dim), v)
+                chosen[list_name(prec, dim)] = v
+            else:
+                todo.append((prec, dim, key))
+        for prec, dim, key in todo:
+            best, best_ms = values[0], float("inf")
+            for v in values:
+                batch.set_option(list_option(prec, dim), v)
+                for _ in range(warmup):
+                    batch.step(nsteps, stream=stream)
+                ms = t(batch, nsteps)
+                if ms < best_ms:
+                    best, best_ms = v, ms
+            batch.set_option(list_option(prec, dim), best)
+            chosen[list_name(prec, dim)] = best
+            self.cache[key] = {0: best}
+        if todo:
+            self._save()
+        return chosen

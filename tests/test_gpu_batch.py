@@ -102,3 +102,31 @@ def test_autotuned_options_are_bitwise_neutral():
             s.step(9)
             for x, y in zip(s.get_state(), want):
                 assert np.array_equal(x, y)
+
+
+def test_tuned_batch_lists_are_bitwise_the_defaults():
+    """The 96-instance batch specification with every N divided by 8 (even,
+    >= 8): the autotuner's per-list CTAs per SM (timed on the GPU) leave every
+    instance's state bitwise that of the library defaults."""
+    from paper_2502_09537_b300 import inputs, tune
+    specs = []
+    for p, _, _ in inputs.batched_instances():
+        n = max(8, (p.N // 8) & ~1)
+        specs.append((p._replace(N=n), KGS_FP64 if len(specs) % 3 else KGS_FP32))
+    states = [random_state(p, 1000 + k, 0.5) for k, (p, _) in enumerate(specs)]
+    results = []
+    for tuned in (False, True):
+        with Batch(1 << 30) as b:
+            ids = [b.add(p, prec) for p, prec in specs]
+            for i, st in zip(ids, states):
+                b.set_state(i, *[a.copy() for a in st])
+            if tuned:
+                chosen = tune.Tuner(None).tune_batch_lists(b, specs, nsteps=2)
+                assert set(chosen) == {"fp64_2d", "fp64_3d", "fp32_2d", "fp32_3d"}
+                for i, st in zip(ids, states):  # tuning stepped them: start again
+                    b.set_state(i, *[a.copy() for a in st])
+            b.step(7)
+            results.append([b.get_state(i) for i in ids])
+    for got, want in zip(results[1], results[0]):
+        for x, y in zip(got, want):
+            assert np.array_equal(x, y)

@@ -91,6 +91,42 @@ def test_tune_batch_sets_best_cta_count():
     assert best == 4 and b.c == 4
 
 
+def test_tune_batch_lists_coordinate_descent_and_cache(tmp_path):
+    """Each list (precision x dimension) of a batch gets its own CTAs per SM:
+    the fake timer rewards FP64 2D lists at 4 and FP32 3D lists at 16 (each
+    list's choice alone matters); the choice is set, returned and cached, and
+    a second tuner reads it without timing."""
+    class FakeBatch:
+        def __init__(self):
+            self.opt = {}
+            self.steps = 0
+
+        def set_option(self, k, v):
+            self.opt[k] = v
+
+        def step(self, n, stream=None):
+            self.steps += 1
+
+    def timer(b, n):
+        return (abs(b.opt.get(tune.list_option(KGS_FP64, 2), 8) - 4)
+                + abs(b.opt.get(tune.list_option(KGS_FP32, 3), 8) - 16) + 1.0)
+
+    members = [(Problem(2, 512, 40, 1, 1, 1, 1, 5e-4), KGS_FP64),
+               (Problem(2, 256, 40, 1, 1, 1, 1, 5e-4), KGS_FP64),
+               (Problem(3, 64, 20, 1, 1, 1, 1, 5e-4), KGS_FP32)]
+    path = str(tmp_path / "t.json")
+    b = FakeBatch()
+    chosen = tune.Tuner(path).tune_batch_lists(b, members, timer=timer)
+    assert chosen == {"fp64_2d": 4, "fp32_3d": 16}
+    assert b.opt[tune.list_option(KGS_FP64, 2)] == 4 and b.opt[tune.list_option(KGS_FP32, 3)] == 16
+    assert b.steps == 8  # one warm-up call per timed value, 4 values x 2 lists
+    b2 = FakeBatch()
+    again = tune.Tuner(path).tune_batch_lists(b2, members, timer=lambda bb, n: 1 / 0)
+    assert again == chosen and b2.opt == b.opt and b2.steps == 0
+    for p, d in ((KGS_FP64, 1), (KGS_FP64, 3), (KGS_FP32, 2)):
+        assert tune.list_name_of_option(tune.list_option(p, d)) == tune.list_name(p, d)
+
+
 def test_serving_request_generator_matches_the_workload_shape():
     from paper_2502_09537_b300 import serve
     reqs = serve.poisson_requests(rate=50.0, count=300, seed=5)
