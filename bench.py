@@ -267,13 +267,15 @@ def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True):
     torch.cuda.synchronize()
     points = sum(p.points for p, _, _ in specs)
     stream = torch.cuda.Stream()
-    tuned_opts = tune.Tuner(tune.default_cache_path()).tune_batch_lists(
-        b, [(p, precision) for p, _, _ in specs], stream=stream) if tuned else {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def load():
         for i, st in zip(ids, init):
             b.set_state(i, *st, stream=stream)
+
+    load()  # the tuner steps the batch: every instance needs a state
+    tuned_opts = tune.Tuner(tune.default_cache_path()).tune_batch_lists(
+        b, [(p, precision) for p, _, _ in specs], stream=stream) if tuned else {}
 
     with torch.cuda.stream(stream):
         for _ in range(warmup):

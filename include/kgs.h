@@ -76,7 +76,12 @@ extern "C" {
                                two colour passes in one cooperative launch whose CTAs take
                                slab chunks in a dependency-safe order (dim 2, 3, N >= 64;
                                KGS_OPT_SLAB_PLANES sets the slab, 0 = about 4 MB of state;
-                               grids it does not fit run the plain passes).  All give
+                               grids it does not fit run the plain passes), 7 streamed planes:
+                               a step's two colour passes in one launch that walks axis 0 with
+                               every plane of a 32 x 64 tile staged by a TMA tensor load
+                               (float32 state, dim 3, N a multiple of 64 up to 1024; allocates
+                               two packed copies of the state, about 2.1 GB each at N = 512, on
+                               first use; other grids run the plain passes).  All give
                                bitwise the same state. */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
 #define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
@@ -107,7 +112,8 @@ extern "C" {
                                    persistent order launch wait for n CTAs that do not exist, and
                                    every dependency wait of the wave kernel and of the
                                    lexicographic sweep for n chunks or steps that do not
-                                   exist, so they time out (after 2 s) and the handle reports
+                                   exist, and makes the streamed-plane kernel wait once on a
+                                   barrier that nothing completes, so they time out (after 2 s) and the handle reports
                                    KGS_ERR_TIMEOUT (kgs_step for the order launch, which waits for
                                    the device; the next synchronising call for the others);
                                    0 (default) off.  For testing the timeout path only. */
@@ -346,7 +352,9 @@ void kgs_batch_destroy(kgs_batch_handle b);
  * KGS_ERR_ARG, CUDA failures KGS_ERR_CUDA (see kgs_last_error).
  * The first call on each device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one scratch array: calls that can
+ * any stream capture.  The address is kept per device and context: after a
+ * cudaDeviceReset (a new context) the next call looks it up again, so make
+ * that call outside a stream capture too.  All calls share the one scratch array: calls that can
  * run at the same time on the GPU (e.g. unordered streams) race and may return
  * wrong values; order them on one stream or with events. */
 #define KGS_NOALLOC_MAX_POINTS 33554432  /* 8192 partial triples x 4096 points each */

@@ -56,6 +56,18 @@ int kgs_probe_nsum(int k, int64_t n, const double* x_host, double beta, double* 
  * call failed. */
 int kgs_probe_psi_weight(int64_t n, const double* r_host, double* w_host, void* stream);
 
+/* Index checks (the stand-in for a memory checker, which this build does not
+ * rely on).  The library built with -DKGS_DEBUG_BOUNDS (libkgs_debug.so)
+ * checks the indices of the colour-pass, streamed-plane and batch kernels
+ * before every access; an index out of range sets a flag bit on the device
+ * and the access is skipped (no trap).  This call synchronises the current
+ * device, writes the OR of the flag bits set since the last call to *flags
+ * (1 colour-pass index, 2 streamed-plane shared-memory index, 4
+ * streamed-plane store, 8 batch index) and clears them.  Returns 1 in the
+ * checking build, 0 in the normal one (where *flags is always 0), -1 for a
+ * NULL flags or -4 if a CUDA call failed. */
+int kgs_debug_bounds(uint32_t* flags);
+
 #ifdef __cplusplus
 }
 #endif

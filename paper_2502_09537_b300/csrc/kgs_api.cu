@@ -98,6 +98,10 @@ struct kgs_solver {
     // for grids lex_sweep_applies takes, the strip sweep's progress counters
     int olex = 0;
     unsigned* lsync = nullptr;
+    // streamed-plane kernel (KGS_OPT_KERNEL 7): two packed copies of the state
+    // and their TMA tensor maps (CUtensorMap storage)
+    void* sbuf[2] = {nullptr, nullptr};
+    alignas(64) unsigned char smap[2][128] = {};
 };
 
 namespace {
@@ -169,7 +173,7 @@ Grid grid_of(const kgs_solver* h)
     return g;
 }
 
-enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5, K_WAVE = 6 };
+enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5, K_WAVE = 6, K_STREAM = 7 };
 
 // Default tile shape per dimension and precision (measured on B300; the batch
 // autotuner can override it per handle).
@@ -189,7 +193,7 @@ TileParams default_tile(int dim, int precision)
 int kernel_choice(const kgs_solver* h)
 {
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
-    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_WAVE) return h->opt_kernel;
+    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_STREAM) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
     // Measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass beats the
     // temporally blocked tiles in both precisions (FP32: 8.6e10 vs 6.2e10 /
@@ -215,6 +219,34 @@ int ensure_tile_buffers(kgs_solver* h)
                     cudaGetErrorString(e));
     }
     return 0;
+}
+
+int ensure_err_word(kgs_solver* h);
+
+// The streamed-plane kernel's packed buffers and tensor maps (first use).
+int ensure_stream(kgs_solver* h)
+{
+    if (h->sbuf[1]) return KGS_OK;
+    if (ensure_err_word(h)) return KGS_ERR_OOM;
+    const size_t bytes = stream_buffer_bytes(h->N);
+    cudaError_t e = cudaMalloc(&h->sbuf[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->sbuf[1], bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->sbuf[0]);
+        h->sbuf[0] = h->sbuf[1] = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA,
+                    "streamed-plane buffers (2 x %zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (stream_make_map(h->sbuf[b], h->N, h->smap[b])) {
+            cudaFree(h->sbuf[0]);
+            cudaFree(h->sbuf[1]);
+            h->sbuf[0] = h->sbuf[1] = nullptr;
+            return fail(KGS_ERR_CUDA, "TMA tensor map of the streamed-plane buffers");
+        }
+    }
+    return KGS_OK;
 }
 
 template <typename T>
@@ -651,6 +683,28 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
         }
         return KGS_OK;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (kc == K_STREAM && stream_applies(h->dim, h->N, h->precision)) {
+            // R_base on the handle's layout, then every (black, red) pair streamed
+            // on the packed copies (the last with the adjoint red half), back
+            int st = ensure_stream(h);
+            if (st) return st;
+            if (pass<T>(h, RED_BASE, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
+            if (launch_to_packed(h->pqb[h->cur], h->uvb[h->cur], h->sbuf[0], h->N, s) < 0)
+                return cuda_fail(h, cudaGetLastError(), "layout conversion");
+            int cs = 0;
+            for (int64_t k = 0; k < nsteps; ++k) {
+                const int mode = k == nsteps - 1 ? RED_ADJ : RED_FUSED;
+                if (launch_stream(h->smap[cs], h->sbuf[cs ^ 1], h->N, h->cf, mode, h->werr, h->opt_stall, s) < 0)
+                    return cuda_fail(h, cudaGetLastError(), "streamed-plane launch");
+                cs ^= 1;
+            }
+            if (launch_from_packed(h->sbuf[cs], h->pqb[h->cur], h->uvb[h->cur], h->N, s) < 0)
+                return cuda_fail(h, cudaGetLastError(), "layout conversion");
+            h->launches += nsteps + 3;
+            return KGS_OK;
+        }
+    }
     if (pass<T>(h, RED_BASE, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
     int64_t pairs = nsteps - 1;
     if (h->opt_graph && pairs >= kGraphPairs) {
@@ -691,6 +745,8 @@ void free_all(kgs_solver* h)
         cudaFree(h->pqb[b]);
         cudaFree(h->uvb[b]);
     }
+    cudaFree(h->sbuf[0]);
+    cudaFree(h->sbuf[1]);
     cudaFree(h->stage);
     cudaFree(h->partials);
     cudaFree(h->out_dev);
@@ -855,6 +911,7 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int 
 
 int kgs_step(kgs_handle h, int64_t nsteps, void* stream)
 {
+    NvtxRange range("kgs_step");
     int st = check_handle(h);
     if (st) return st;
     if (nsteps < 0) return fail(KGS_ERR_ARG, "nsteps must be >= 0");
@@ -994,6 +1051,7 @@ int kgs_order_levels(kgs_handle h, int64_t* nlevels)
 
 int kgs_invariants(kgs_handle h, double* out3, void* stream)
 {
+    NvtxRange range("kgs_invariants");
     int st = check_handle(h);
     if (st) return st;
     if (!out3) return fail(KGS_ERR_ARG, "NULL output");
@@ -1054,7 +1112,7 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     if (st) return st;
     switch (option) {
     case KGS_OPT_KERNEL:
-        if (value < 0 || value > 6) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 6");
+        if (value < 0 || value > 7) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 7");
         if (value == 5 && h->dim < 2) return fail(KGS_ERR_ARG, "the slab kernel needs dim 2 or 3");
         if (value == 6 && h->dim < 2) return fail(KGS_ERR_ARG, "the wave kernel needs dim 2 or 3");
         if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))

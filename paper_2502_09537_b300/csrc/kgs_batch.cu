@@ -37,6 +37,11 @@
 
 using namespace kgs;
 
+namespace kgs {
+KGS_BOUNDS_TU
+KGS_BOUNDS_READER(bounds_flags_batch)
+}  // namespace kgs
+
 namespace {
 
 constexpr int kChunk = 256;  // colour points per work item (= CTA size)
@@ -113,6 +118,12 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int pa
     const I own = (parity ? half : 0) + (i >> 1);
     const I oth = parity ? 0 : half;
     T* u = reinterpret_cast<T*>(in.uv);
+    {
+        bool ok = own >= 0 && own < 2 * half;
+#pragma unroll
+        for (int m = 0; m < 2 * D; ++m) ok = ok && oth + (nb[m] >> 1) >= 0 && oth + (nb[m] >> 1) < 2 * half;
+        if (!kgs::kgs_in_bounds(ok, 8u)) return;
+    }
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
@@ -768,6 +779,7 @@ int kgs_batch_get_state(kgs_batch_handle b, int64_t id, double* P, double* Q, do
 
 int kgs_batch_step_each(kgs_batch_handle b, const int64_t* nsteps, void* stream)
 {
+    NvtxRange range("kgs_batch_step");
     int st = bcheck(b);
     if (st) return st;
     if (!nsteps) return bfail(KGS_ERR_ARG, "NULL step counts");
@@ -794,6 +806,7 @@ int kgs_batch_step(kgs_batch_handle b, int64_t nsteps, void* stream)
 
 int kgs_batch_invariants(kgs_batch_handle b, int64_t id, double* out3, void* stream)
 {
+    NvtxRange range("kgs_batch_invariants");
     int st = bcheck(b);
     if (st) return st;
     if ((st = inst_check(b, id))) return st;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -94,6 +95,27 @@ int64_t tile_smem_bytes(int dim, int elem_bytes, const TileParams& tp);
 template <typename T>
 int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<T>* uv,
                 vec2_t<T>* pq_out, vec2_t<T>* uv_out, const Coef<T>& c, cudaStream_t stream);
+
+// Streamed planes (kgs_stream.cu): float32 3D step pairs, a step's black and
+// red passes in one launch walking axis 0, planes staged by TMA tensor loads,
+// on a private packed layout (per colour and plane, (N + 4) rows of N/2 + 4
+// float4 (P, Q, U, V), with ghost copies of the periodic neighbours).
+// stream_applies: whether a grid qualifies; stream_buffer_bytes: one packed
+// copy of the state; stream_make_map: the TMA tensor map (a 64-byte aligned,
+// 128-byte CUtensorMap at map_out) of a packed buffer, 0 or -1.
+// launch_stream: one step pair (BLACK_FUSED, red_mode = RED_FUSED or
+// RED_ADJ) reading the buffer of `map`, writing dst; err: the word a CTA sets
+// to 2 if a bounded wait ran out (stall != 0 makes every CTA wait once on a
+// barrier nothing completes).  launch_to_packed / launch_from_packed: the
+// whole state between the colour-split layout and a packed buffer.  Each
+// returns 1 (kernels launched) or -1 if a launch failed.
+bool stream_applies(int dim, int64_t N, int precision);
+size_t stream_buffer_bytes(int64_t N);
+int stream_make_map(void* buf, int64_t N, void* map_out);
+int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, int red_mode, int* err, int stall,
+                  cudaStream_t s);
+int launch_to_packed(const void* pq, const void* uv, void* out, int64_t N, cudaStream_t s);
+int launch_from_packed(const void* in, void* pq, void* uv, int64_t N, cudaStream_t s);
 
 // Update orders (kgs_order.cu).  order_schedule: level of every point of a
 // permutation `order` of the N^dim grid (returns 0, -1 if order is not a
@@ -221,6 +243,50 @@ inline Coef<float> host_coef32(const Coef<double>& c)
     f.hs = (float)c.hs;
     return f;
 }
+
+// Index checks of the KGS_DEBUG_BOUNDS build (libkgs_debug.so).  With the
+// macro defined, a kernel checks its indices before an access and, where one
+// is out of range, sets a bit of its file's device flag word and skips the
+// access instead of trapping (the flags are read and cleared by
+// kgs_debug_bounds, kgs_probe.h); without it the checks compile to nothing.
+// Bits: 1 colour-pass indices, 2 streamed-plane shared-memory indices, 4
+// streamed-plane stores, 8 batch indices.  KGS_BOUNDS_TU defines the flag
+// word and kgs_in_bounds in a file, KGS_BOUNDS_READER(fn) its host reader.
+#ifdef KGS_DEBUG_BOUNDS
+#define KGS_BOUNDS_TU                                                                 \
+    static __device__ unsigned kgs_bounds_flag_;                                     \
+    static __device__ __forceinline__ bool kgs_in_bounds(bool ok, unsigned bit)      \
+    {                                                                                 \
+        if (!ok) atomicOr(&kgs_bounds_flag_, bit);                                    \
+        return ok;                                                                    \
+    }
+#define KGS_BOUNDS_READER(fn)                                                         \
+    unsigned fn()                                                                     \
+    {                                                                                 \
+        unsigned v = 0, z = 0;                                                        \
+        if (cudaMemcpyFromSymbol(&v, kgs_bounds_flag_, sizeof v) != cudaSuccess) return ~0u; \
+        if (cudaMemcpyToSymbol(kgs_bounds_flag_, &z, sizeof z) != cudaSuccess) return ~0u;   \
+        return v;                                                                     \
+    }
+#else
+#define KGS_BOUNDS_TU                                                                 \
+    static __device__ __forceinline__ bool kgs_in_bounds(bool, unsigned) { return true; }
+#define KGS_BOUNDS_READER(fn) \
+    unsigned fn() { return 0u; }
+#endif
+unsigned bounds_flags_sweep();
+unsigned bounds_flags_stream();
+unsigned bounds_flags_batch();
+
+// An NVTX range over a scope (kgs_step, kgs_invariants, the batch calls): a
+// profiler attached to the process shows each call on its timeline; without
+// one the push and pop return at once (NVTX v3, header only).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Record status and message as the calling thread's last error (what
 // kgs_last_status / kgs_last_error return); returns status.

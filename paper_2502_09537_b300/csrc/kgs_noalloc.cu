@@ -18,6 +18,8 @@
 // so nothing has to start at zero, but all calls share the one array: calls
 // that can overlap on the GPU (different streams without ordering between
 // them) race and may return wrong values.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -40,6 +42,10 @@ static __device__ __align__(256) double g_noalloc_partials[3 * kMaxCtas];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_partials_addr[kMaxDevices] = {};
+// the context each address was looked up in: a device reset replaces the
+// device's context (and the module's copy of the array), so the address is
+// looked up again when the current context differs
+void* g_partials_ctx[kMaxDevices] = {};
 
 struct Acc {
     double s, c;
@@ -137,7 +143,28 @@ __global__ void __launch_bounds__(kThreads) noalloc_finalize_kernel(const double
         for (int k = 0; k < 3; ++k) out3[k] = (red[k][0].s + red[k][0].c) * hd;
 }
 
-// Resolve the scratch array's device address for the current device (once).
+// The calling thread's current driver context (nullptr if none or unknown),
+// through the driver entry point the runtime exposes: no link to libcuda.
+void* current_context()
+{
+    using CtxGetCurrent = CUresult (*)(CUcontext*);
+    static CtxGetCurrent fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrent>(f);
+        looked = true;
+    }
+    CUcontext ctx = nullptr;
+    if (!fn || fn(&ctx) != CUDA_SUCCESS) return nullptr;
+    return ctx;
+}
+
+// Resolve the scratch array's device address for the current device: once per
+// device and context (again after a device reset, which replaces the context).
 int scratch_address(double** out)
 {
     int dev = -1;
@@ -146,12 +173,14 @@ int scratch_address(double** out)
     if (dev < 0 || dev >= kMaxDevices)
         return kgs::report_error(KGS_ERR_RANGE, "device index beyond the supported 64");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_partials_addr[dev] || !ctx || ctx != g_partials_ctx[dev]) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
         if (e != cudaSuccess || !ptr)
             return kgs::report_error(KGS_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
         g_partials_addr[dev] = static_cast<double*>(ptr);
+        g_partials_ctx[dev] = current_context();  // now current, if it was not before the lookup
     }
     *out = g_partials_addr[dev];
     return KGS_OK;

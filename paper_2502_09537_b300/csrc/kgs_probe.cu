@@ -6,7 +6,7 @@
 
 #include <cuda_runtime.h>
 
-#include "kgs_point.cuh"
+#include "kgs_internal.h"
 
 namespace {
 
@@ -143,4 +143,21 @@ extern "C" int kgs_probe_fma_rate(int precision, int64_t iters, int blocks_per_s
     if (precision == 64) return run<double>(iters, blocks_per_sm, (cudaStream_t)stream, elapsed_ms, fma_per_s);
     if (precision == 32) return run<float>(iters, blocks_per_sm, (cudaStream_t)stream, elapsed_ms, fma_per_s);
     return -1;
+}
+
+extern "C" int kgs_debug_bounds(uint32_t* flags)
+{
+    if (!flags) return -1;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -4;
+    const unsigned f[3] = {kgs::bounds_flags_sweep(), kgs::bounds_flags_stream(), kgs::bounds_flags_batch()};
+    *flags = 0;
+    for (unsigned v : f) {
+        if (v == ~0u) return -4;
+        *flags |= v;
+    }
+#ifdef KGS_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
 }

@@ -18,6 +18,9 @@
 
 namespace kgs {
 
+KGS_BOUNDS_TU
+KGS_BOUNDS_READER(bounds_flags_sweep)
+
 // Linear index of the t-th point of the colour whose 0-based index sum has
 // parity `parity`, and its 2*D periodic neighbours in the order
 // (axis 0 down, axis 0 up, axis 1 down, ...).  Rows run along the last axis;
@@ -148,6 +151,12 @@ __device__ __forceinline__ void pass_point(vec2_t<T>* pq, vec2_t<T>* uv, int N, 
     const I own = (parity ? half : 0) + (i >> 1);
     const I oth = parity ? 0 : half;
     T* u = reinterpret_cast<T*>(uv);  // planar: U at a position, V at 2 half + position
+    {
+        bool ok = own >= 0 && own < 2 * half;
+#pragma unroll
+        for (int m = 0; m < 2 * D; ++m) ok = ok && oth + (nb[m] >> 1) >= 0 && oth + (nb[m] >> 1) < 2 * half;
+        if (!kgs_in_bounds(ok, 1u)) return;
+    }
     T p[2 * D], q[2 * D], w[2 * D];
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {

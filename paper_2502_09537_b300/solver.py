@@ -16,7 +16,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libkgs.so")
+# KGS_LIBRARY may name another build of the same ABI (the index-checking
+# libkgs_debug.so of build.build(debug_bounds=True)).
+LIB_PATH = os.environ.get("KGS_LIBRARY") or os.path.join(HERE, "libkgs.so")
 
 KGS_OK = 0
 KGS_HOST = 0
@@ -83,6 +85,7 @@ SIGNATURES = {
     "kgs_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, _c_int64, ctypes.c_int, _vp, _dp, _dp]),
     "kgs_probe_nsum": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _c_dbl, _vp, _vp, _vp, _vp]),
     "kgs_probe_psi_weight": (ctypes.c_int, [_c_int64, _vp, _vp, _vp]),
+    "kgs_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
 }
 
 _lib = None
@@ -99,7 +102,7 @@ def load_library():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libkgs.so not built at {LIB_PATH}; run "
+            raise ImportError(f"libkgs not built at {LIB_PATH}; run "
                               "`python -m paper_2502_09537_b300.build`")
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
@@ -108,6 +111,15 @@ def load_library():
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def debug_bounds():
+    """(checking build?, flag bits set since the last call) of kgs_debug_bounds."""
+    f = ctypes.c_uint32()
+    r = load_library().kgs_debug_bounds(ctypes.byref(f))
+    if r < 0:
+        raise KGSError(r, "kgs_debug_bounds failed")
+    return bool(r), int(f.value)
 
 
 def last_error() -> str:

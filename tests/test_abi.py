@@ -43,6 +43,18 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in solver.SIGNATURES, f"binding lacks {n}"
 
 
+def test_debug_bounds_library_exports_the_same_abi():
+    """The index-checking build (KGS_DEBUG_BOUNDS) exports every declared
+    function too, and kgs_debug_bounds tells the two builds apart without a
+    GPU call reaching a device (the normal build answers 0 before any)."""
+    path = kbuild.build(debug_bounds=True)
+    dbg = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(dbg, n), n
+    out = os.popen(f"/usr/local/cuda/bin/cuobjdump --list-elf {path} 2>&1").read()
+    assert "sm_103a" in out
+
+
 def test_library_is_built_for_sm103a(lib):
     out = os.popen(f"/usr/local/cuda/bin/cuobjdump --list-elf {kbuild.LIB} 2>&1").read()
     assert "sm_103a" in out
