@@ -485,9 +485,12 @@ def configure(s, args, prob):
     for flag, opt in ((args.threads, ks.KGS_OPT_THREADS), (args.kernel, ks.KGS_OPT_KERNEL),
                       (args.ppt, ks.KGS_OPT_PPT), (args.slab_planes, ks.KGS_OPT_SLAB_PLANES),
                       (args.wave_lag, ks.KGS_OPT_WAVE_LAG), (args.wave_chunk, ks.KGS_OPT_WAVE_CHUNK),
-                      (args.order_mode, ks.KGS_OPT_ORDER_MODE)):
+                      (args.order_mode, ks.KGS_OPT_ORDER_MODE),
+                      (args.stream_chunk, ks.KGS_OPT_STREAM_CHUNK)):
         if flag:
             s.set_option(opt, flag)
+    if args.stream_prefetch >= 0:
+        s.set_option(ks.KGS_OPT_STREAM_PREFETCH, args.stream_prefetch)
     if args.pdl >= 0:
         s.set_option(ks.KGS_OPT_PDL, args.pdl)
     if args.order == "lex-rev":
@@ -644,6 +647,9 @@ def main():
                          "5 slab-pipelined passes, 6 wave (a step's two passes in one launch), "
                          "7 streamed planes (3D FP32: a step's two passes per axis-0 plane, TMA-staged)")
     ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab and wave kernels)")
+    ap.add_argument("--stream-chunk", type=int, default=0, help="KGS_OPT_STREAM_CHUNK (streamed-plane kernel)")
+    ap.add_argument("--stream-prefetch", type=int, default=-1,
+                    help="KGS_OPT_STREAM_PREFETCH (streamed-plane kernel; -1: the library default)")
     ap.add_argument("--wave-lag", type=int, default=0, help="KGS_OPT_WAVE_LAG (wave kernel)")
     ap.add_argument("--wave-chunk", type=int, default=0, help="KGS_OPT_WAVE_CHUNK (wave kernel)")
     ap.add_argument("--pdl", type=int, default=-1, help="KGS_OPT_PDL (-1: the library default)")
@@ -697,7 +703,7 @@ def main():
                    "threads": args.threads or 256, "kernel": args.kernel, "order": args.order,
                    "order_mode": args.order_mode,
                    "slab_planes": args.slab_planes, "wave_lag": args.wave_lag,
-                   "wave_chunk": args.wave_chunk,
+                   "wave_chunk": args.wave_chunk, "stream_chunk": args.stream_chunk,
                    "tau": prob.tau, "steps_per_solve": work.nsteps, "precision": args.precision,
                    "energy_every": ENERGY_EVERY,
                    "l2": "256 MB buffer written between timed steps",

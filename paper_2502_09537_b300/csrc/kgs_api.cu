@@ -102,6 +102,8 @@ struct kgs_solver {
     // and their TMA tensor maps (CUtensorMap storage)
     void* sbuf[2] = {nullptr, nullptr};
     alignas(64) unsigned char smap[2][128] = {};
+    int opt_stream_chunk = 0;  // KGS_OPT_STREAM_CHUNK
+    int opt_stream_prefetch = -1;  // KGS_OPT_STREAM_PREFETCH (-1: default)
 };
 
 namespace {
@@ -195,10 +197,14 @@ int kernel_choice(const kgs_solver* h)
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
     if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_STREAM) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
-    // Measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass beats the
-    // temporally blocked tiles in both precisions (FP32: 8.6e10 vs 6.2e10 /
-    // 9.8e10 vs 3.4e10 point-updates/s; FP64: 1.0e10 vs 6.1e9), so the tile
-    // kernel is chosen only on request (KGS_OPT_KERNEL = 3).
+    // Float32 3D grids the streamed-plane kernel takes: a step's two passes in
+    // one read and one write of the state (measured at 512^3: 1.257e11
+    // point-updates/s, 0.72 of HBM, against 1.085e11 for two pass launches).
+    if (stream_applies(h->dim, h->N, h->precision)) return K_STREAM;
+    // Otherwise, measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass
+    // beats the temporally blocked tiles in both precisions (FP32: 8.6e10 vs
+    // 6.2e10 / 9.8e10 vs 3.4e10 point-updates/s; FP64: 1.0e10 vs 6.1e9), so
+    // the tile kernel is chosen only on request (KGS_OPT_KERNEL = 3).
     return K_PASS;
 }
 
@@ -695,13 +701,18 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
             int cs = 0;
             for (int64_t k = 0; k < nsteps; ++k) {
                 const int mode = k == nsteps - 1 ? RED_ADJ : RED_FUSED;
-                if (launch_stream(h->smap[cs], h->sbuf[cs ^ 1], h->N, h->cf, mode, h->werr, h->opt_stall, s) < 0)
+                // 64-plane chunks by default (measured at 512^3: 0.724 of HBM against
+                // 0.699 for contiguous shares and 0.698 for 32-plane chunks)
+                const int chunk = h->opt_stream_chunk == 0 ? 64 : (h->opt_stream_chunk < 0 ? 0 : h->opt_stream_chunk);
+                const int pf = h->opt_stream_prefetch < 0 ? 2 : h->opt_stream_prefetch;
+                if (launch_stream(h->smap[cs], h->sbuf[cs ^ 1], h->N, h->cf, mode, h->werr, h->opt_stall, chunk, pf,
+                                  s) < 0)
                     return cuda_fail(h, cudaGetLastError(), "streamed-plane launch");
                 cs ^= 1;
             }
             if (launch_from_packed(h->sbuf[cs], h->pqb[h->cur], h->uvb[h->cur], h->N, s) < 0)
                 return cuda_fail(h, cudaGetLastError(), "layout conversion");
-            h->launches += nsteps + 3;
+            h->launches += nsteps + 2;  // (the R_base pass counted itself)
             return KGS_OK;
         }
     }
@@ -1185,6 +1196,14 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
             return fail(KGS_ERR_ARG, "KGS_OPT_THREADS takes 128, 256 or 512");
         h->opt_threads = (int)value;
         drop_graph(h);
+        return KGS_OK;
+    case KGS_OPT_STREAM_CHUNK:
+        if (value < -1 || value > 65536) return fail(KGS_ERR_ARG, "KGS_OPT_STREAM_CHUNK takes -1 to 65536");
+        h->opt_stream_chunk = (int)value;
+        return KGS_OK;
+    case KGS_OPT_STREAM_PREFETCH:
+        if (value < 0 || value > 16) return fail(KGS_ERR_ARG, "KGS_OPT_STREAM_PREFETCH takes 0 to 16");
+        h->opt_stream_prefetch = (int)value;
         return KGS_OK;
     case KGS_OPT_PDL:
         if (value < 0 || value > 1) return fail(KGS_ERR_ARG, "KGS_OPT_PDL takes 0 or 1");

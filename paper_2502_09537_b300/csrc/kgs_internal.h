@@ -106,14 +106,17 @@ int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<
 // launch_stream: one step pair (BLACK_FUSED, red_mode = RED_FUSED or
 // RED_ADJ) reading the buffer of `map`, writing dst; err: the word a CTA sets
 // to 2 if a bounded wait ran out (stall != 0 makes every CTA wait once on a
-// barrier nothing completes).  launch_to_packed / launch_from_packed: the
+// barrier nothing completes).  chunk: 0 = each CTA a contiguous share of
+// the (tile, plane) sequence; > 0 = items of `chunk` planes round-robin in
+// chunk-major order (neighbouring tiles in step); prefetch: planes beyond
+// the shared-memory loads also fetched into L2 (0: none).  launch_to_packed / launch_from_packed: the
 // whole state between the colour-split layout and a packed buffer.  Each
 // returns 1 (kernels launched) or -1 if a launch failed.
 bool stream_applies(int dim, int64_t N, int precision);
 size_t stream_buffer_bytes(int64_t N);
 int stream_make_map(void* buf, int64_t N, void* map_out);
 int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, int red_mode, int* err, int stall,
-                  cudaStream_t s);
+                  int chunk, int prefetch, cudaStream_t s);
 int launch_to_packed(const void* pq, const void* uv, void* out, int64_t N, cudaStream_t s);
 int launch_from_packed(const void* in, void* pq, void* uv, int64_t N, cudaStream_t s);
 

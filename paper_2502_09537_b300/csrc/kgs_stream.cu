@@ -66,7 +66,7 @@ constexpr int kTy = 32;                  // tile rows (axis 1)
 constexpr int kRR = kTy + 4, kKK = kTh + 4;  // staged rows / columns per colour
 constexpr int kSlotElems = 2 * kRR * kKK;    // float4 per staged plane
 constexpr int kSlots = 5;
-constexpr int kWarps = 18;               // black pass: (kTy + 4) row tasks over 18 warps = 2 each
+constexpr int kWarps = kTy;              // warp t: tile row t (its black, then its red point)
 constexpr int kThreads = 32 * kWarps;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr size_t kSmemBytes = (size_t)kSlots * kSlotElems * sizeof(float4) + (kSlots + 1) * sizeof(uint64_t);
@@ -126,27 +126,12 @@ __device__ __forceinline__ void tma_load_plane(float4* dst, const CUtensorMap* m
         : "memory");
 }
 
-// Store a point of colour c at (x, y, zh) of the packed layout, with its
-// ghost copies (the periodic images two rows / two columns beyond the edges).
-__device__ __forceinline__ void store_packed(float4* __restrict__ dst, int N, int c, int x, int y, int zh,
-                                             float4 v)
+// The same box into L2 only (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_plane(const CUtensorMap* map, int c0, int c1, int c2)
 {
-    const int hN = N >> 1;
-    const int64_t cols = hN + 4, rows = N + 4;
-    float4* plane = dst + ((int64_t)c * N + x) * rows * cols;
-    const int pr = y + 2, pc = zh + 2;
-    const int pr2 = y < 2 ? y + N + 2 : (y >= N - 2 ? y - N + 2 : -1);
-    const int pc2 = zh < 2 ? zh + hN + 2 : (zh >= hN - 2 ? zh - hN + 2 : -1);
-    if (!kgs_in_bounds(c >= 0 && c < 2 && x >= 0 && x < N && pr < rows && pc < cols && pr2 < rows && pc2 < cols &&
-                           y >= 0 && zh >= 0,
-                       4u))
-        return;
-    plane[pr * cols + pc] = v;
-    if (pr2 >= 0) plane[pr2 * cols + pc] = v;
-    if (pc2 >= 0) {
-        plane[pr * cols + pc2] = v;
-        if (pr2 >= 0) plane[pr2 * cols + pc2] = v;
-    }
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(map), "r"(c0),
+                 "r"(c1), "r"(c2), "r"(0)
+                 : "memory");
 }
 
 // One point of colour `own_c` at staged (r, k) of plane slot `s` updated in
@@ -181,15 +166,16 @@ __device__ __forceinline__ float4 stream_point(const float4* s, const float4* dn
 template <int REDMODE>
 __global__ void __launch_bounds__(kThreads, 1)
     stream_kernel(const __grid_constant__ CUtensorMap src, float4* __restrict__ dst, int N, Coef<float> c, int* err,
-                  int stall)
+                  int stall, int chunk, int pf)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4* slots = reinterpret_cast<float4*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kSlots * kSlotElems * sizeof(float4));
     constexpr int cR = 0, cB = 1;  // 3D: red = even 0-based coordinate sum (red_parity(3) == 0)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;  // warp t: tile row t
     const int hN = N >> 1;
     const int tiles_z = hN / kTh, ntiles = (N / kTy) * tiles_z;
+    const int64_t cols = hN + 4, plane_elems = (int64_t)(N + 4) * cols;
     if (threadIdx.x == 0) {
         for (int s = 0; s <= kSlots; ++s) mbar_init(&bars[s], 1);  // bars[kSlots]: the stall test's
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -198,17 +184,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;    // bit s: parity of slot s's next completion (same in every thread)
     uint32_t pending = 0;  // thread 0: slots with a load in flight
     int failed = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    bool first = true;
+    // This CTA's work, as segments (planes [x0, x0 + L) of one tile).  chunk = 0:
+    // a contiguous share of the (tile, axis-0 plane) sequence, tile-major (one
+    // or two segments per CTA).  chunk > 0: items of `chunk` planes taken
+    // round-robin in chunk-major order, so that CTAs on neighbouring tiles
+    // stream the same planes at about the same time and the halo rows they
+    // share are read from L2 by the second.
+    const int64_t W = (int64_t)ntiles * N;
+    int64_t w0 = (int64_t)blockIdx.x * W / gridDim.x;
+    const int64_t w1 = (int64_t)(blockIdx.x + 1) * W / gridDim.x;
+    const int nchunks = chunk > 0 ? (N + chunk - 1) / chunk : 0;
+    int64_t item = blockIdx.x;
+    for (;;) {
+        int tile, x0, L;
+        if (chunk > 0) {
+            if (item >= (int64_t)nchunks * ntiles || failed) break;
+            tile = (int)(item % ntiles);
+            x0 = (int)(item / ntiles) * chunk;
+            L = N - x0 < chunk ? N - x0 : chunk;
+            item += gridDim.x;
+        } else {
+            if (w0 >= w1 || failed) break;
+            tile = (int)(w0 / N);
+            x0 = (int)(w0 % N);
+            L = (int)((w1 - w0) < (int64_t)(N - x0) ? (w1 - w0) : (int64_t)(N - x0));
+            w0 += L;
+        }
         const int y0 = (tile / tiles_z) * kTy, zh0 = (tile % tiles_z) * kTh;
-        // staged plane j (0 .. N+3) is axis-0 plane j - 2 mod N, in slot j % kSlots
+        // staged plane j (0 .. L + 3) is axis-0 plane x0 - 2 + j mod N, in slot j % kSlots
+        auto coords = [&](int j) {
+            int p = x0 - 2 + j;
+            return p < 0 ? p + N : (p >= N ? p - N : p);
+        };
         auto issue = [&](int j) {
             const int s = j % kSlots;
-            int p = j - 2;
-            p = p < 0 ? p + N : (p >= N ? p - N : p);
             mbar_expect_tx(&bars[s], (unsigned)(kSlotElems * sizeof(float4)));
-            tma_load_plane(slots + s * kSlotElems, &src, &bars[s], 4 * zh0, y0, p);
+            tma_load_plane(slots + s * kSlotElems, &src, &bars[s], 4 * zh0, y0, coords(j));
             pending |= 1u << s;
         };
+        auto prefetch = [&](int j) { tma_prefetch_plane(&src, 4 * zh0, y0, coords(j)); };
         auto wait = [&](int j) -> bool {
             const int s = j % kSlots;
             const bool ok = mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
@@ -218,64 +233,85 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             return ok;
         };
+        // this thread's red point (tile row t, colour column lane) in the packed
+        // output: its offset in a plane and those of its ghost copies (-1: none)
+        const int y = y0 + t, zh = zh0 + lane;
+        const int pr2 = y < 2 ? y + N + 2 : (y >= N - 2 ? y - N + 2 : -1);
+        const int pc2 = zh < 2 ? zh + hN + 2 : (zh >= hN - 2 ? zh - hN + 2 : -1);
+        const int64_t off0 = (int64_t)(y + 2) * cols + zh + 2;
+        const int64_t offr = pr2 >= 0 ? (int64_t)pr2 * cols + zh + 2 : -1;
+        const int64_t offc = pc2 >= 0 ? (int64_t)(y + 2) * cols + pc2 : -1;
+        const int64_t offrc = (pr2 >= 0 && pc2 >= 0) ? (int64_t)pr2 * cols + pc2 : -1;
+        auto store = [&](int col, int x, float4 v) {
+            float4* pl = dst + ((int64_t)col * N + x) * plane_elems;
+            if (!kgs_in_bounds(x >= 0 && x < N && off0 < plane_elems && offr < plane_elems && offc < plane_elems &&
+                                   offrc < plane_elems,
+                               4u))
+                return;
+            pl[off0] = v;
+            if (offr >= 0) pl[offr] = v;
+            if (offc >= 0) pl[offc] = v;
+            if (offrc >= 0) pl[offrc] = v;
+        };
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int j = 0; j < kSlots - 1; ++j) issue(j);
+            for (int j = 0; j < kSlots - 1 && j <= L + 3; ++j) issue(j);
+            for (int j = kSlots - 1; j < kSlots - 1 + pf && j <= L + 3; ++j) prefetch(j);
         }
         int bad = 0;
         for (int j = 0; j < 3; ++j) bad |= !wait(j);
         failed = __syncthreads_or(bad);
-        for (int cb = -1; cb <= N && !failed; ++cb) {
-            // black pass on plane cb (staged j = cb + 2); red neighbours in j = cb + 1, cb + 3
-            {
-                const float4* s = slots + ((cb + 2) % kSlots) * kSlotElems;
-                const float4* dn = slots + ((cb + 1) % kSlots) * kSlotElems;
-                const float4* up = slots + ((cb + 3) % kSlots) * kSlotElems;
-                float4* sw = slots + ((cb + 2) % kSlots) * kSlotElems + cB * kRR * kKK;
-                for (int t = warp; t < kTy + 4; t += kWarps) {
-                    int r, k;
-                    if (t < kTy) {
-                        r = 2 + t;
-                        k = 2 + lane;
-                    } else if (t < kTy + 2) {
-                        r = t == kTy ? 1 : kTy + 2;
-                        k = 2 + lane;
-                    } else {
-                        r = 2 + lane;
-                        k = t == kTy + 2 ? 1 : kTh + 2;
-                    }
-                    // black (colour 1) at axis-0 plane cb, row y0 - 2 + r (y0 even)
-                    const int zp = (cB ^ cb ^ r) & 1;
-                    sw[r * kKK + k] = stream_point<BLACK_FUSED>(s, dn, up, cB, r, k, zp, c);
-                }
-            }
-            __syncthreads();
-            // red pass on plane cb - 1 (staged j = cb + 1); black neighbours in j = cb, cb + 2
-            if (cb >= 1) {
+        const int r = 2 + t, k = 2 + lane;
+        for (int it = 0; it <= L + 1 && !failed; ++it) {
+            const int cb = x0 - 1 + it;  // black plane; red plane cb - 1
+            // black pass on plane cb (staged j = it + 1), red neighbours in j = it, it + 2:
+            // this thread's interior point (r, k)
+            const float4* sb = slots + ((it + 1) % kSlots) * kSlotElems;
+            const float4* sbd = slots + (it % kSlots) * kSlotElems;
+            const float4* sbu = slots + ((it + 2) % kSlots) * kSlotElems;
+            float4* wb = const_cast<float4*>(sb) + cB * kRR * kKK;
+            wb[r * kKK + k] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, r, k, (cB ^ cb ^ r) & 1, c);
+            // red pass on plane cb - 1 (staged j = it), black neighbours in j = it - 1, it + 1:
+            // its point (r, k) needs black (cb) only at (r, k), just written by this thread
+            if (it >= 2) {
                 const int x = cb - 1;
-                const float4* s = slots + ((cb + 1) % kSlots) * kSlotElems;
-                const float4* dn = slots + (cb % kSlots) * kSlotElems;
-                const float4* up = slots + ((cb + 2) % kSlots) * kSlotElems;
-                for (int t = warp; t < kTy; t += kWarps) {
-                    const int r = 2 + t, k = 2 + lane;
-                    const int zp = (cR ^ x ^ r) & 1;
-                    const float4 a = stream_point<REDMODE>(s, dn, up, cR, r, k, zp, c);
-                    const int y = y0 + t, zh = zh0 + lane;
-                    store_packed(dst, N, cR, x, y, zh, a);
-                    store_packed(dst, N, cB, x, y, zh, s[cB * kRR * kKK + r * kKK + k]);
-                }
+                const float4* sr = slots + (it % kSlots) * kSlotElems;
+                const float4* srd = slots + ((it + kSlots - 1) % kSlots) * kSlotElems;
+                const float4 a = stream_point<REDMODE>(sr, srd, sb, cR, r, k, (cR ^ x ^ r) & 1, c);
+                store(cR, x, a);
+                store(cB, x, sr[cB * kRR * kKK + r * kKK + k]);
             }
-            // the next black pass needs staged plane cb + 4
+            // the ring of black points of plane cb that the red pass of plane cb
+            // reads (next iteration): rows 1 and kTy + 2, and per row the one
+            // column beyond the tile on the side its red points' last-axis
+            // neighbours fall
+            if (t < 3) {
+                int rr, kk;
+                if (t < 2) {
+                    rr = t == 0 ? 1 : kTy + 2;
+                    kk = 2 + lane;
+                } else {
+                    rr = 2 + lane;
+                    kk = ((cb ^ rr) & 1) ? kTh + 2 : 1;
+                }
+                wb[rr * kKK + kk] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, rr, kk, (cB ^ cb ^ rr) & 1, c);
+            }
+            // the next black pass needs staged plane it + 4 (it + 3 for its upper neighbours)
             bad = 0;
-            if (stall && cb == 0) bad = !mbar_wait_bounded(&bars[kSlots], 0);  // never completes
-            if (!bad && cb + 4 <= N + 3) bad = !wait(cb + 4);
+            if (stall && first && it == 1) bad = !mbar_wait_bounded(&bars[kSlots], 0);  // never completes
+            if (!bad && it + 3 <= L + 3) bad = !wait(it + 3);
             failed = __syncthreads_or(bad);
-            // staged plane cb (axis-0 plane cb - 2) is no longer read: load plane cb + 5 into its slot
-            if (!failed && threadIdx.x == 0 && cb + 5 <= N + 3) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(cb + 5);
+            // staged plane it - 1 is no longer read: load plane it + 4 into its slot, and
+            // prefetch plane it + 4 + pf into L2 (pf planes beyond the loads)
+            if (!failed && threadIdx.x == 0) {
+                if (it + 4 <= L + 3) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(it + 4);
+                }
+                if (pf > 0 && it + 4 + pf <= L + 3) prefetch(it + 4 + pf);
             }
         }
+        first = false;
     }
     if (failed && threadIdx.x == 0) {
         *(volatile int*)err = 2;
@@ -368,14 +404,17 @@ int stream_make_map(void* buf, int64_t N, void* map_out)
     const cuuint64_t strides[3] = {row, row * (cuuint64_t)(N + 4), row * (cuuint64_t)(N + 4) * (cuuint64_t)N};
     const cuuint32_t box[4] = {4 * kKK, kRR, 1, 2};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
+    // a staged row is 4 kKK floats = 576 bytes = 9 x 64: L2 promotion to 64-byte
+    // lines fetches exactly the row (256-byte promotion read 768 bytes per row,
+    // measured: 1.54x the algorithmic DRAM reads per launch at 512^3)
     CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
 int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, int red_mode, int* err, int stall,
-                  cudaStream_t s)
+                  int chunk, int prefetch, cudaStream_t s)
 {
     static bool attr_set[2] = {false, false};
     auto kern = red_mode == RED_ADJ ? stream_kernel<RED_ADJ> : stream_kernel<RED_FUSED>;
@@ -388,11 +427,13 @@ int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, i
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ntiles = (int)((N / kTy) * (N / 2 / kTh));
-    const unsigned grid = (unsigned)std::min(ntiles, sms);
+    const int64_t ntiles = (N / kTy) * (N / 2 / kTh);
+    const int64_t items = chunk > 0 ? ntiles * ((N + chunk - 1) / chunk) : ntiles * N;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
     CUtensorMap m;
     memcpy(&m, map, sizeof m);
-    kern<<<grid, kThreads, kSmemBytes, s>>>(m, reinterpret_cast<float4*>(dst), (int)N, c, err, stall);
+    kern<<<grid, kThreads, kSmemBytes, s>>>(m, reinterpret_cast<float4*>(dst), (int)N, c, err, stall, chunk,
+                                            prefetch);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

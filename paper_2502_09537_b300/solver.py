@@ -40,6 +40,8 @@ KGS_OPT_TEST_BARRIER_STALL = 12
 KGS_OPT_WAVE_LAG = 13
 KGS_OPT_WAVE_CHUNK = 14
 KGS_OPT_PDL = 15
+KGS_OPT_STREAM_CHUNK = 16
+KGS_OPT_STREAM_PREFETCH = 17
 KGS_ERR_TIMEOUT = -6
 
 # Every function the header declares, with its ctypes signature.

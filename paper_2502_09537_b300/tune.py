@@ -29,7 +29,7 @@ from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
 from .solver import (KGS_BATCH_OPT_CTAS_LIST, KGS_BATCH_OPT_CTAS_PER_SM, KGS_FP64, KGS_OPT_KERNEL, KGS_OPT_THREADS,
                      KGS_OPT_TILE_LX, KGS_OPT_TILE_PASSES, KGS_OPT_TILE_T1, KGS_OPT_TILE_T2,
-                     KGS_OPT_TILE_THREADS)
+                     KGS_OPT_TILE_THREADS, KGS_OPT_STREAM_CHUNK)
 
 SMEM_BYTES = 227 * 1024
 Options = Dict[int, int]
@@ -55,6 +55,9 @@ def candidates(prob, precision: int) -> List[Options]:
     out.append({KGS_OPT_KERNEL: 4})  # persistent grid-stride passes
     if prob.dim >= 2:
         out.append({KGS_OPT_KERNEL: 5})  # colour passes pipelined in L2-sized axis-0 slabs
+    if prob.dim == 3 and precision != KGS_FP64 and prob.N % 64 == 0 and 64 <= prob.N <= 1024:
+        # streamed planes: a step's two passes in one launch, in chunk orders
+        out += [{KGS_OPT_KERNEL: 7, KGS_OPT_STREAM_CHUNK: ch} for ch in (0, 32, 128, -1)]
     if prob.points <= SMEM_BYTES // (4 * elem):
         out.append({KGS_OPT_KERNEL: 2})
     if prob.dim == 2:

@@ -20,9 +20,11 @@ from paper_2502_09537_b300.solver import KGS_FP32, KGS_FP64, KGS_OPT_KERNEL, Sol
 STREAM = 7
 
 
-def run(prob, st, splits, kernel, precision=KGS_FP32):
+def run(prob, st, splits, kernel, precision=KGS_FP32, chunk=0):
+    from paper_2502_09537_b300.solver import KGS_OPT_STREAM_CHUNK
     with Solver.from_problem(prob, precision) as s:
         s.set_option(KGS_OPT_KERNEL, kernel)
+        s.set_option(KGS_OPT_STREAM_CHUNK, chunk)
         s.set_state(*[np.array(a, copy=True) for a in st])
         for n in splits:
             s.step(n)
@@ -31,14 +33,36 @@ def run(prob, st, splits, kernel, precision=KGS_FP32):
 
 @pytest.mark.parametrize("N", [64, 128, 192])
 @pytest.mark.parametrize("splits", [[1], [2], [7], [3, 4]])
-def test_streamed_planes_are_bitwise_the_pass_kernel(N, splits):
+@pytest.mark.parametrize("chunk", [-1, 0, 5, 128])
+def test_streamed_planes_are_bitwise_the_pass_kernel(N, splits, chunk):
+    """Both work orders: contiguous shares (chunk -1) and round-robin chunks
+    (the default 64 planes; a ragged last chunk for 5; whole tiles for 128
+    at N <= 128)."""
     prob = Problem(3, N, 20.0, 1.1, 0.9, 1.2, 0.8, 5e-4 * (512 / N) ** 2)
     st = random_state(prob, 2502_09537 + 300 + N, 0.5)
     want, inv_want = run(prob, st, [sum(splits)], 1)
-    got, inv_got = run(prob, st, splits, STREAM)
+    got, inv_got = run(prob, st, splits, STREAM, chunk=chunk)
     for x, y in zip(got, want):
         assert np.array_equal(x, y)
     assert inv_got == inv_want
+
+
+def test_streamed_planes_are_the_default_for_fp32_3d():
+    """KGS_OPT_KERNEL 0 (auto) takes the streamed planes for a float32 3D grid
+    it fits: bitwise kernel 7's state and launch count."""
+    prob = Problem(3, 64, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
+    st = random_state(prob, 2502_09537 + 311, 0.5)
+    counts = []
+    for kernel in (0, STREAM):
+        with Solver.from_problem(prob, KGS_FP32) as s:
+            s.set_option(KGS_OPT_KERNEL, kernel)
+            s.set_state(*[np.array(a, copy=True) for a in st])
+            l0 = s.launch_count
+            s.step(6)
+            counts.append((s.launch_count - l0, s.get_state()))
+    assert counts[0][0] == counts[1][0] == 6 + 3
+    for x, y in zip(counts[0][1], counts[1][1]):
+        assert np.array_equal(x, y)
 
 
 def test_streamed_planes_negative_kappa1_and_bumps():
