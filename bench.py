@@ -72,22 +72,50 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
     return 3 * (2 * dim - 1) + 57.5
 
 
-# DRAM bytes per launch of the dominant kernel (a fused colour pass): the sum
-# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of that
-# launch on the workload's full grid (2D: a RED_FUSED pass of the 2048^2
-# grid; 3D: a pass launch of the 512^3 grid, one-pass metrics), for the
-# kernels as they are now; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("2d", "fp64"): 117.52e6 + 25.74e6,
-               ("3d", "fp64"): 3.7645e9 + 2.1086e9,
-               ("3d", "fp32"): 1.8822e9 + 1.0321e9}
+# DRAM bytes per launch of the dominant kernel: the sum dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of that launch on the workload's
+# full grid (2D: a RED_FUSED pass of the 2048^2 grid; 3D: a launch of the
+# 512^3 grid, one-pass metrics), for the kernels as they are now, keyed by
+# (workload, precision, kernel: "pass" = one launch per colour pass, "stream"
+# = a step's two passes per launch); None where no capture exists.
+NCU_TRAFFIC = {("2d", "fp64", "pass"): 117.52e6 + 25.74e6,
+               ("3d", "fp64", "pass"): 3.7645e9 + 2.1086e9,
+               ("3d", "fp32", "pass"): 1.8822e9 + 1.0321e9,
+               ("3d", "fp32", "stream"): 2.2837e9 + 2.1558e9}
+
+
+# Issue-slot view of the float64 colour passes: the fraction of peak each
+# pipe issued at (sm__inst_executed_pipe_{fp64,alu,fma}, smsp__issue_active;
+# ncu --set full, active cycles, mean of the black and red passes), from the
+# captures of the current kernels: 2D on the 2048^2 launches, 3D on 256^3
+# launches.  The FP64 pipe binds; the integer ALU pipe, which carries the
+# exact neighbour sums and the Psi weight, is close behind.
+NCU_PIPES = {("2d", "fp64", "pass"): {"fp64": 0.874, "alu": 0.746, "fma": 0.129, "issue_active": 0.611},
+             ("3d", "fp64", "pass"): {"fp64": 0.864, "alu": 0.825, "fma": 0.131, "issue_active": 0.652}}
+
+
+def kernel_name(args, precision=None):
+    """The dominant kernel of a solve: what KGS_OPT_KERNEL selects (0 = the
+    library's automatic choice, which streams float32 3D grids whose N is a
+    multiple of 64, up to 1024, and makes one launch per pass otherwise)."""
+    precision = precision or args.precision
+    n = args.grid_n or {"1d": 512, "2d": 2048, "3d": 512}.get(args.workload, 0)
+    streams = args.workload == "3d" and precision == "fp32" and n % 64 == 0 and 64 <= n <= 1024
+    if args.kernel == 7 or (args.kernel == 0 and streams):
+        return "stream" if streams else "pass"
+    return "pass" if args.kernel in (0, 1) else None
+
 
 def traffic_of(args, precision=None):
-    """DRAM bytes per pass launch from the ncu captures above: only for the
-    launches they were taken on (the default one-per-pass kernel on the
-    workload's full grid, checkerboard order); None otherwise."""
-    if args.order != "checkerboard" or args.kernel not in (0, 1) or args.grid_n:
+    """DRAM bytes per launch of the dominant kernel from the ncu captures
+    above: only for the launches they were taken on (the workload's full grid,
+    checkerboard order, the kernel captured); None otherwise."""
+    if args.order != "checkerboard" or args.grid_n:
         return None
-    return NCU_TRAFFIC.get((args.workload, precision or args.precision))
+    k = kernel_name(args, precision)
+    if k is None:
+        return None
+    return NCU_TRAFFIC.get((args.workload, precision or args.precision, k))
 
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
@@ -571,6 +599,11 @@ def solo_leg(args, work, precision_name, init_dev, flush, local, dist, world, st
                 / (pass_ms * 1e-3) / 1e12,
                 "hbm_frac": bytes_per_point_update(elem) * upd_per_launch / (pass_ms * 1e-3)
                 / 1e9 / peaks.get("hbm_gbs", 6400.0)}
+        k = kernel_name(args, precision_name)
+        if traffic_of(args, precision_name) is not None and (args.workload, precision_name, k) in NCU_PIPES:
+            roof["pipes_ncu"] = dict(NCU_PIPES[(args.workload, precision_name, k)],
+                                     note="fraction of each pipe's peak issue rate over active cycles, "
+                                          "ncu capture of these launches")
     else:
         achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)

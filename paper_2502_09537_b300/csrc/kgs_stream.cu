@@ -12,16 +12,22 @@
 // plane ahead of the red pass (Sec. 4.2: no point has a neighbour of its own
 // colour, so each pass updates its plane's points in any order).
 //
-// Work: a CTA owns a tile of 32 x 64 points of the other two axes (32 rows
-// along axis 1, 32 points of each colour along the last axis) and walks every
-// axis-0 plane of it, periodically: planes -2 .. N+1 are staged, black is
-// updated on planes -1 .. N and red on planes 0 .. N-1, the two ends
-// recomputing the neighbouring planes' black values from the same inputs (so
-// bitwise the values their owner computes).  Within a plane the black pass
-// covers the tile and the ring of black points around it that the tile's red
-// points read, which needs the red points of a two-point ring: each staged
+// Work: a tile is 32 x 64 points of the other two axes (32 rows along axis 1,
+// 32 points of each colour along the last axis).  One CTA per SM takes work
+// items of 64 consecutive axis-0 planes of a tile, round-robin in chunk-major
+// order, so that CTAs on neighbouring tiles stream the same planes at about
+// the same time and the halo rows they share come from L2 for the second.
+// For an item's planes [x0, x0 + L) it stages planes x0-2 .. x0+L+1 (mod N),
+// updates black on x0-1 .. x0+L and red on x0 .. x0+L-1; the black values of
+// the two outer planes are recomputed from the same inputs as their owner's,
+// so bitwise the same.  Within a plane the black pass covers the tile and the
+// ring of black points that the tile's red points read (two rows, and per row
+// the one column beyond the tile on the side its red points' last-axis
+// neighbours fall), which needs a two-point ring of red points: each staged
 // plane is the tile plus a two-point halo, (32 + 4) x (32 + 4) points of each
-// colour.
+// colour.  Warp t owns tile row t: each thread updates its black point of
+// plane i, then the red point of plane i-1 at the same position, which reads
+// black plane i only there -- the thread's own value.
 //
 // Data: the state lives, for the launches of a kgs_step call, in a private
 // packed layout: per colour (0-based coordinate-sum parity) and axis-0 plane,
@@ -36,13 +42,14 @@
 // Conversions from and to the handle's colour-split layout run once per
 // kgs_step call.
 //
-// Ring: five slots; the load of plane j + 5 goes into the slot of plane j
-// once the step at plane j + 2 is done with it, a full plane iteration before
-// it is needed.  Two CTA barriers per plane: between the black and the red
-// pass, and after the red pass (where the next plane's load is also awaited).
-// Every wait on an mbarrier is bounded (2 s of %globaltimer); a CTA whose wait
-// runs out sets the error word, waits (bounded) for its loads in flight and
-// leaves.
+// Ring: five slots, four planes in use and the next in flight; the load of
+// staged plane j + 5 goes into the slot of plane j once the red pass of plane
+// j + 1 is done with it, a full plane iteration before it is needed, and
+// planes further ahead are prefetched into L2 (KGS_OPT_STREAM_PREFETCH).  One
+// CTA barrier per plane, after both passes, where the next plane's load is
+// also awaited.  Every wait on an mbarrier is bounded (2 s of %globaltimer); a
+// CTA whose wait runs out sets the error word, waits (bounded) for its loads
+// in flight and leaves.
 //
 // Every point update is update_point (kgs_point.cuh) with the neighbour order
 // of the one-launch-per-pass kernel, so the state is bitwise that of two pass

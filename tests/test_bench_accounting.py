@@ -47,14 +47,21 @@ def _args(**kw):
 
 
 def test_traffic_only_for_the_captured_launches(bench):
-    assert bench.traffic_of(_args()) == bench.NCU_TRAFFIC[("2d", "fp64")]
-    assert bench.traffic_of(_args(kernel=1, workload="3d", precision="fp32")) == bench.NCU_TRAFFIC[("3d", "fp32")]
+    T = bench.NCU_TRAFFIC
+    assert bench.traffic_of(_args()) == T[("2d", "fp64", "pass")]
+    assert bench.traffic_of(_args(kernel=1, workload="3d", precision="fp32")) == T[("3d", "fp32", "pass")]
+    # auto on a float32 3D grid streams; so does kernel 7
+    assert bench.kernel_name(_args(workload="3d", precision="fp32")) == "stream"
+    assert bench.traffic_of(_args(workload="3d", precision="fp32")) == T[("3d", "fp32", "stream")]
+    assert bench.traffic_of(_args(kernel=7, workload="3d", precision="fp32")) == T[("3d", "fp32", "stream")]
+    assert bench.kernel_name(_args(kernel=7, workload="3d", precision="fp64")) == "pass"
+    assert bench.traffic_of(_args(workload="3d")) == T[("3d", "fp64", "pass")]
     assert bench.traffic_of(_args(kernel=6)) is None          # another kernel
     assert bench.traffic_of(_args(kernel=5)) is None
     assert bench.traffic_of(_args(grid_n=256)) is None        # another grid size
     assert bench.traffic_of(_args(order="lex")) is None       # another update order
     assert bench.traffic_of(_args(workload="1d")) is None     # never captured
-    for v in bench.NCU_TRAFFIC.values():
+    for v in T.values():
         assert v is None or v > 0
 
 
