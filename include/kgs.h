@@ -78,7 +78,7 @@ extern "C" {
                                KGS_OPT_SLAB_PLANES sets the slab, 0 = about 4 MB of state;
                                grids it does not fit run the plain passes), 7 streamed planes:
                                a step's two colour passes in one launch that walks axis 0 with
-                               every plane of a 32 x 64 tile staged by a TMA tensor load
+                               every plane of a 29 x 64 tile staged by a TMA tensor load
                                (float32 state, dim 3, N a multiple of 64 up to 1024; allocates
                                two packed copies of the state, about 2.2 GB each at N = 512, on
                                first use; other grids run the plain passes).  Auto picks 2 for

@@ -12,22 +12,25 @@
 // plane ahead of the red pass (Sec. 4.2: no point has a neighbour of its own
 // colour, so each pass updates its plane's points in any order).
 //
-// Work: a tile is 32 x 64 points of the other two axes (32 rows along axis 1,
-// 32 points of each colour along the last axis).  One CTA per SM takes work
-// items of 64 consecutive axis-0 planes of a tile, round-robin in chunk-major
-// order, so that CTAs on neighbouring tiles stream the same planes at about
-// the same time and the halo rows they share come from L2 for the second.
-// For an item's planes [x0, x0 + L) it stages planes x0-2 .. x0+L+1 (mod N),
-// updates black on x0-1 .. x0+L and red on x0 .. x0+L-1; the black values of
-// the two outer planes are recomputed from the same inputs as their owner's,
-// so bitwise the same.  Within a plane the black pass covers the tile and the
-// ring of black points that the tile's red points read (two rows, and per row
-// the one column beyond the tile on the side its red points' last-axis
-// neighbours fall), which needs a two-point ring of red points: each staged
-// plane is the tile plus a two-point halo, (32 + 4) x (32 + 4) points of each
-// colour.  Warp t owns tile row t: each thread updates its black point of
-// plane i, then the red point of plane i-1 at the same position, which reads
-// black plane i only there -- the thread's own value.
+// Work: a tile is 29 x 64 points of the other two axes (29 rows along axis 1,
+// 32 points of each colour along the last axis; the last tile of a grid has
+// the rows that are left).  One CTA per SM takes work items of 64 consecutive
+// axis-0 planes of a tile, round-robin in chunk-major order, so that CTAs on
+// neighbouring tiles stream the same planes at about the same time and the
+// halo rows they share come from L2 for the second.  For an item's planes
+// [x0, x0 + L) it stages planes x0-2 .. x0+L+1 (mod N), updates black on
+// x0-1 .. x0+L and red on x0 .. x0+L-1; the black values of the two outer
+// planes are recomputed from the same inputs as their owner's, so bitwise the
+// same.  Within a plane the black pass covers the tile and the ring of black
+// points that the tile's red points read (two rows, and per row the one column
+// beyond the tile on the side its red points' last-axis neighbours fall), which
+// needs a two-point ring of red points: each staged plane is the tile plus a
+// two-point halo, (29 + 4) x (32 + 4) points of each colour (rows beyond the
+// grid, in a short last tile, are zero-filled by the load and never read).
+// Warp t < 29 owns tile row t: each thread updates its black point of plane i,
+// then the red point of plane i-1 at the same position, which reads black
+// plane i only there -- the thread's own value; the other three warps update
+// the ring, so every warp has at most two point updates per plane.
 //
 // Data: the state lives, for the launches of a kgs_step call, in a private
 // packed layout: per colour (0-based coordinate-sum parity) and axis-0 plane,
@@ -42,9 +45,9 @@
 // Conversions from and to the handle's colour-split layout run once per
 // kgs_step call.
 //
-// Ring: five slots, four planes in use and the next in flight; the load of
-// staged plane j + 5 goes into the slot of plane j once the red pass of plane
-// j + 1 is done with it, a full plane iteration before it is needed, and
+// Ring: six slots of 38 KB, four planes in use and two in flight; the load of
+// staged plane j + 6 goes into the slot of plane j once the red pass of plane
+// j + 1 is done with it, two plane iterations before it is needed, and
 // planes further ahead are prefetched into L2 (KGS_OPT_STREAM_PREFETCH).  One
 // CTA barrier per plane, after both passes, where the next plane's load is
 // also awaited.  Every wait on an mbarrier is bounded (2 s of %globaltimer); a
@@ -69,11 +72,11 @@ KGS_BOUNDS_READER(bounds_flags_stream)
 namespace {
 
 constexpr int kTh = 32;                  // colour points per tile row (= warp lanes)
-constexpr int kTy = 32;                  // tile rows (axis 1)
+constexpr int kTy = 29;                  // tile rows (axis 1); the last tile of a grid may be shorter
 constexpr int kRR = kTy + 4, kKK = kTh + 4;  // staged rows / columns per colour
 constexpr int kSlotElems = 2 * kRR * kKK;    // float4 per staged plane
-constexpr int kSlots = 5;
-constexpr int kWarps = kTy;              // warp t: tile row t (its black, then its red point)
+constexpr int kSlots = 6;
+constexpr int kWarps = 32;               // warp t < kTy: tile row t; warps kTy .. kTy+2: the ring
 constexpr int kThreads = 32 * kWarps;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr size_t kSmemBytes = (size_t)kSlots * kSlotElems * sizeof(float4) + (kSlots + 1) * sizeof(uint64_t);
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int cR = 0, cB = 1;  // 3D: red = even 0-based coordinate sum (red_parity(3) == 0)
     const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;  // warp t: tile row t
     const int hN = N >> 1;
-    const int tiles_z = hN / kTh, ntiles = (N / kTy) * tiles_z;
+    const int tiles_z = hN / kTh, ntiles = ((N + kTy - 1) / kTy) * tiles_z;
     const int64_t cols = hN + 4, plane_elems = (int64_t)(N + 4) * cols;
     if (threadIdx.x == 0) {
         for (int s = 0; s <= kSlots; ++s) mbar_init(&bars[s], 1);  // bars[kSlots]: the stall test's
@@ -219,6 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             w0 += L;
         }
         const int y0 = (tile / tiles_z) * kTy, zh0 = (tile % tiles_z) * kTh;
+        const int ty = N - y0 < kTy ? N - y0 : kTy;  // the tile's rows
+        const int yp = y0 & 1;  // staged row r is axis-1 coordinate y0 - 2 + r, of parity yp ^ (r & 1)
         // staged plane j (0 .. L + 3) is axis-0 plane x0 - 2 + j mod N, in slot j % kSlots
         auto coords = [&](int j) {
             int p = x0 - 2 + j;
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         // this thread's red point (tile row t, colour column lane) in the packed
         // output: its offset in a plane and those of its ghost copies (-1: none)
-        const int y = y0 + t, zh = zh0 + lane;
+        const int y = y0 + (t < ty ? t : 0), zh = zh0 + lane;  // rows t >= ty have no point
         const int pr2 = y < 2 ? y + N + 2 : (y >= N - 2 ? y - N + 2 : -1);
         const int pc2 = zh < 2 ? zh + hN + 2 : (zh >= hN - 2 ? zh - hN + 2 : -1);
         const int64_t off0 = (int64_t)(y + 2) * cols + zh + 2;
@@ -277,45 +282,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float4* sbd = slots + (it % kSlots) * kSlotElems;
             const float4* sbu = slots + ((it + 2) % kSlots) * kSlotElems;
             float4* wb = const_cast<float4*>(sb) + cB * kRR * kKK;
-            wb[r * kKK + k] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, r, k, (cB ^ cb ^ r) & 1, c);
+            if (t < ty) wb[r * kKK + k] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, r, k, (cB ^ cb ^ yp ^ r) & 1, c);
             // red pass on plane cb - 1 (staged j = it), black neighbours in j = it - 1, it + 1:
             // its point (r, k) needs black (cb) only at (r, k), just written by this thread
-            if (it >= 2) {
+            if (it >= 2 && t < ty) {
                 const int x = cb - 1;
                 const float4* sr = slots + (it % kSlots) * kSlotElems;
                 const float4* srd = slots + ((it + kSlots - 1) % kSlots) * kSlotElems;
-                const float4 a = stream_point<REDMODE>(sr, srd, sb, cR, r, k, (cR ^ x ^ r) & 1, c);
+                const float4 a = stream_point<REDMODE>(sr, srd, sb, cR, r, k, (cR ^ x ^ yp ^ r) & 1, c);
                 store(cR, x, a);
                 store(cB, x, sr[cB * kRR * kKK + r * kKK + k]);
             }
             // the ring of black points of plane cb that the red pass of plane cb
-            // reads (next iteration): rows 1 and kTy + 2, and per row the one
+            // reads (next iteration): rows 1 and ty + 2, and per row the one
             // column beyond the tile on the side its red points' last-axis
-            // neighbours fall
-            if (t < 3) {
+            // neighbours fall -- by the three warps that own no tile row
+            if (t >= kTy && (t < kTy + 2 || lane < ty)) {
                 int rr, kk;
-                if (t < 2) {
-                    rr = t == 0 ? 1 : kTy + 2;
+                if (t < kTy + 2) {
+                    rr = t == kTy ? 1 : ty + 2;
                     kk = 2 + lane;
                 } else {
                     rr = 2 + lane;
-                    kk = ((cb ^ rr) & 1) ? kTh + 2 : 1;
+                    kk = ((cb ^ yp ^ rr) & 1) ? kTh + 2 : 1;
                 }
-                wb[rr * kKK + kk] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, rr, kk, (cB ^ cb ^ rr) & 1, c);
+                wb[rr * kKK + kk] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, rr, kk, (cB ^ cb ^ yp ^ rr) & 1, c);
             }
-            // the next black pass needs staged plane it + 4 (it + 3 for its upper neighbours)
+            // the next black pass needs staged plane it + 3 (its upper neighbours)
             bad = 0;
             if (stall && first && it == 1) bad = !mbar_wait_bounded(&bars[kSlots], 0);  // never completes
             if (!bad && it + 3 <= L + 3) bad = !wait(it + 3);
             failed = __syncthreads_or(bad);
-            // staged plane it - 1 is no longer read: load plane it + 4 into its slot, and
-            // prefetch plane it + 4 + pf into L2 (pf planes beyond the loads)
+            // staged plane it - 1 is no longer read: load plane it - 1 + kSlots into its
+            // slot, and prefetch the plane pf beyond it into L2
             if (!failed && threadIdx.x == 0) {
-                if (it + 4 <= L + 3) {
+                if (it + kSlots - 1 <= L + 3) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(it + 4);
+                    issue(it + kSlots - 1);
                 }
-                if (pf > 0 && it + 4 + pf <= L + 3) prefetch(it + 4 + pf);
+                if (pf > 0 && it + kSlots - 1 + pf <= L + 3) prefetch(it + kSlots - 1 + pf);
             }
         }
         first = false;
@@ -434,7 +439,7 @@ int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, i
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ntiles = (N / kTy) * (N / 2 / kTh);
+    const int64_t ntiles = ((N + kTy - 1) / kTy) * (N / 2 / kTh);
     const int64_t items = chunk > 0 ? ntiles * ((N + chunk - 1) / chunk) : ntiles * N;
     const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
     CUtensorMap m;
