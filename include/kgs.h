@@ -49,7 +49,11 @@ extern "C" {
 #define KGS_OK            0
 #define KGS_ERR_ARG      -1  /* invalid argument (dim, L, parameters, NULL pointer, where) */
 #define KGS_ERR_ODD_N    -2  /* N odd or N < 4: the periodic checkerboard needs even N */
-#define KGS_ERR_OOM      -3  /* device allocation failed */
+#define KGS_ERR_OOM      -3  /* device allocation failed (or would take the handle past
+                                  KGS_DEVICE_BUDGET: an environment variable, in bytes, read by
+                                  kgs_create; it caps what one handle allocates -- its state and
+                                  the buffers options add on first use -- so that the out-of-
+                                  memory paths can be exercised without exhausting the device) */
 #define KGS_ERR_CUDA     -4  /* a CUDA call failed (also: no usable device) */
 #define KGS_ERR_STATE    -5  /* no state set yet */
 #define KGS_ERR_TIMEOUT  -6  /* a bounded device wait ran out (a grid barrier of the persistent

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -103,6 +104,9 @@ struct kgs_solver {
     void* sbuf[2] = {nullptr, nullptr};
     alignas(64) unsigned char smap[2][128] = {};
     int opt_stream_chunk = 0;  // KGS_OPT_STREAM_CHUNK
+    // device bytes this handle may allocate (KGS_DEVICE_BUDGET at creation; 0 =
+    // no limit) and the bytes it holds
+    size_t budget = 0, dev_bytes = 0;
     int opt_stream_prefetch = -1;  // KGS_OPT_STREAM_PREFETCH (-1: default)
 };
 
@@ -143,6 +147,29 @@ int check_handle(kgs_solver* h)
 }
 
 bool is_finite_(double x) { return std::isfinite(x); }
+
+// A device allocation of the handle, counted against its budget: with the
+// environment variable KGS_DEVICE_BUDGET set (bytes, read by kgs_create) an
+// allocation that would take the handle past it fails on the host as if the
+// device were out of memory -- the way to make an allocation fail on purpose
+// (tests of the KGS_ERR_OOM paths) without exhausting a shared device.
+cudaError_t hmalloc(kgs_solver* h, void** p, size_t bytes)
+{
+    if (h->budget && h->dev_bytes + bytes > h->budget) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) h->dev_bytes += bytes;
+    return e;
+}
+
+void hfree(kgs_solver* h, void* p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    h->dev_bytes -= bytes < h->dev_bytes ? bytes : h->dev_bytes;
+}
 
 void compute_coef(kgs_solver* h)
 {
@@ -213,11 +240,11 @@ int ensure_tile_buffers(kgs_solver* h)
     if (h->pqb[1]) return 0;
     const size_t elem = h->precision == 64 ? sizeof(double2) : sizeof(float2);
     const size_t bytes = (size_t)h->M * elem;
-    cudaError_t e = cudaMalloc(&h->pqb[1], bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->uvb[1], bytes);
+    cudaError_t e = hmalloc(h, &h->pqb[1], bytes);
+    if (e == cudaSuccess) e = hmalloc(h, &h->uvb[1], bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(h->pqb[1]);
+        hfree(h, h->pqb[1], bytes);
         h->pqb[1] = nullptr;
         h->uvb[1] = nullptr;
         return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA,
@@ -235,19 +262,19 @@ int ensure_stream(kgs_solver* h)
     if (h->sbuf[1]) return KGS_OK;
     if (ensure_err_word(h)) return KGS_ERR_OOM;
     const size_t bytes = stream_buffer_bytes(h->N);
-    cudaError_t e = cudaMalloc(&h->sbuf[0], bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->sbuf[1], bytes);
+    cudaError_t e = hmalloc(h, &h->sbuf[0], bytes);
+    if (e == cudaSuccess) e = hmalloc(h, &h->sbuf[1], bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(h->sbuf[0]);
+        hfree(h, h->sbuf[0], bytes);
         h->sbuf[0] = h->sbuf[1] = nullptr;
         return fail(e == cudaErrorMemoryAllocation ? KGS_ERR_OOM : KGS_ERR_CUDA,
                     "streamed-plane buffers (2 x %zu bytes): %s", bytes, cudaGetErrorString(e));
     }
     for (int b = 0; b < 2; ++b) {
         if (stream_make_map(h->sbuf[b], h->N, h->smap[b])) {
-            cudaFree(h->sbuf[0]);
-            cudaFree(h->sbuf[1]);
+            hfree(h, h->sbuf[0], bytes);
+            hfree(h, h->sbuf[1], bytes);
             h->sbuf[0] = h->sbuf[1] = nullptr;
             return fail(KGS_ERR_CUDA, "TMA tensor map of the streamed-plane buffers");
         }
@@ -828,11 +855,12 @@ kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kap
     const size_t elem = precision == 64 ? sizeof(double2) : sizeof(float2);
     const size_t state_bytes = (size_t)h->M * elem;
     h->nblocks = invariants_blocks(h->dim, h->N);
-    cudaError_t ea = cudaMalloc(&h->pqb[0], state_bytes);
-    if (ea == cudaSuccess) ea = cudaMalloc(&h->uvb[0], state_bytes);
-    if (ea == cudaSuccess) ea = cudaMalloc(&h->stage, (size_t)h->M * sizeof(double));
-    if (ea == cudaSuccess) ea = cudaMalloc(&h->partials, (size_t)h->nblocks * 3 * sizeof(double));
-    if (ea == cudaSuccess) ea = cudaMalloc(&h->out_dev, 3 * sizeof(double));
+    if (const char* b = std::getenv("KGS_DEVICE_BUDGET")) h->budget = (size_t)std::strtoull(b, nullptr, 10);
+    cudaError_t ea = hmalloc(h, &h->pqb[0], state_bytes);
+    if (ea == cudaSuccess) ea = hmalloc(h, &h->uvb[0], state_bytes);
+    if (ea == cudaSuccess) ea = hmalloc(h, (void**)&h->stage, (size_t)h->M * sizeof(double));
+    if (ea == cudaSuccess) ea = hmalloc(h, (void**)&h->partials, (size_t)h->nblocks * 3 * sizeof(double));
+    if (ea == cudaSuccess) ea = hmalloc(h, (void**)&h->out_dev, 3 * sizeof(double));
     if (ea == cudaSuccess) ea = cudaMallocHost(&h->out_host, 3 * sizeof(double));
     if (ea != cudaSuccess) {
         cudaGetLastError();
