@@ -272,7 +272,7 @@ def init_dist():
     return world, rank, local, dist
 
 
-def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True):
+def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True, persistent=False):
     """The 96-instance batch: 64 2D grids N in {128..2048} and 32 3D grids N in
     {64..256}, random parameters, tau = 5e-4, 500 steps, every instance in the
     chosen precision, stepped by kgs_batch_step (one launch per colour pass,
@@ -288,6 +288,9 @@ def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True):
     nsteps = specs[0][1]
     total_bytes = sum(p.points * 4 * elem for p, _, _ in specs)
     b = Batch(int(total_bytes * 1.05) + (64 << 20))
+    if persistent:
+        from paper_2502_09537_b300.solver import KGS_BATCH_OPT_PERSISTENT
+        b.set_option(KGS_BATCH_OPT_PERSISTENT, 1)
     init, ids = [], []
     for p, _, fn in specs:
         ids.append(b.add(p, precision))
@@ -303,7 +306,7 @@ def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True):
 
     load()  # the tuner steps the batch: every instance needs a state
     tuned_opts = tune.Tuner(tune.default_cache_path()).tune_batch_lists(
-        b, [(p, precision) for p, _, _ in specs], stream=stream) if tuned else {}
+        b, [(p, precision) for p, _, _ in specs], stream=stream) if tuned and not persistent else {}
 
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -364,7 +367,7 @@ def batch_leg(precision_name, steps, warmup, world, local, dist, tuned=True):
         "dtype": "f64" if elem == 8 else "f32",
         "config": {"workload": "kgs_batch96", "instances": len(specs), "points": points,
                    "steps_per_solve": nsteps, "precision": precision_name,
-                   "tuned": tuned_opts,
+                   "tuned": tuned_opts, "persistent_launch": bool(persistent),
                    "l2": "256 MB buffer written between timed steps"},
         "roofline": roof,
         "e2e": {"value": world * points * nsteps / e2e_s, "unit": UNIT,
@@ -377,7 +380,8 @@ def run_batch(args):
     world, rank, local, dist = init_dist()
     from paper_2502_09537_b300 import build as kbuild
     kbuild.build()
-    leg = batch_leg(args.precision, args.steps, args.warmup, world, local, dist, tuned=not args.untuned)
+    leg = batch_leg(args.precision, args.steps, args.warmup, world, local, dist, tuned=not args.untuned,
+                    persistent=args.batch_persistent)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
     line.update(leg)
@@ -674,6 +678,8 @@ def main():
     ap.add_argument("--no-summaries", action="store_true",
                     help="3d: skip the compact batch and serve summaries")
     ap.add_argument("--untuned", action="store_true", help="batch: library defaults, no autotuner")
+    ap.add_argument("--batch-persistent", action="store_true",
+                    help="batch: one persistent cooperative launch per step call (KGS_BATCH_OPT_PERSISTENT)")
     ap.add_argument("--threads", type=int, default=0, help="colour-pass CTA size (tuning)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent, "

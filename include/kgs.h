@@ -306,6 +306,18 @@ typedef struct kgs_batch* kgs_batch_handle;
  * 3 p + (dim - 1), p = 0 for FP64 and 1 for FP32, value 1..32, or 0 to follow
  * KGS_BATCH_OPT_CTAS_PER_SM again (which also resets every list). */
 #define KGS_BATCH_OPT_CTAS_LIST   16
+/* 1: each kgs_batch_step / step_each call is one persistent cooperative launch
+ * (in the CUDA graph, when graphs are on) that runs every colour pass of every
+ * instance, both precisions and every dimension, with a bounded grid barrier
+ * between passes (a wait past 2 s makes the batch report KGS_ERR_TIMEOUT from
+ * its next call on); CTAs per SM: KGS_BATCH_OPT_CTAS_PER_SM, at most what fits.
+ * Batches with an instance of 2^31 points or more take the per-pass launches.
+ * 0 (default): one launch per colour pass, precision, dimension and mode, the
+ * lists on their own streams.  Bitwise the same states either way. */
+#define KGS_BATCH_OPT_PERSISTENT  3
+/* test hook: n > 0 makes the persistent launch's grid barrier wait for n CTAs
+ * that do not exist, so that it times out (KGS_ERR_TIMEOUT); 0 (default) off. */
+#define KGS_BATCH_OPT_TEST_STALL  4
 
 /* Create a batch on `device` (-1 = current) with an arena of capacity_bytes
  * (>= 4096).  NULL on error (kgs_last_status / kgs_last_error). */

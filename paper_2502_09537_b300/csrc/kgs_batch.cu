@@ -109,7 +109,10 @@ __device__ __forceinline__ I batch_point(I t, int N, int parity, I nb[2 * D])
 // An instance's state is in the colour-split layout of a handle's
 // (kgs_internal.h): this colour's half from pq + own, the neighbours in the
 // other half, U and V planar in the (U,V) buffer.
-template <typename T, int D, int MODE, typename I>
+// COHERENT: read the other colour's values with loads that bypass L1 (.cg),
+// for the persistent kernel, where other CTAs wrote them during the same
+// launch (L1 is not coherent across SMs); otherwise the read-only path.
+template <typename T, int D, int MODE, typename I, bool COHERENT = false>
 __device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int parity)
 {
     I nb[2 * D];
@@ -128,13 +131,13 @@ __device__ __forceinline__ void batch_update(const BatchInst<T>& in, I t, int pa
 #pragma unroll
     for (int m = 0; m < 2 * D; ++m) {
         const I k = oth + (nb[m] >> 1);
-        const vec2_t<T> b = __ldg(&in.pq[k]);
+        const vec2_t<T> b = COHERENT ? __ldcg(&in.pq[k]) : __ldg(&in.pq[k]);
         p[m] = b.x;
         q[m] = b.y;
-        w[m] = __ldg(&u[k]);
+        w[m] = COHERENT ? __ldcg(&u[k]) : __ldg(&u[k]);
     }
-    vec2_t<T> a = in.pq[own];
-    T U = u[own], V = u[2 * half + own];
+    vec2_t<T> a = COHERENT ? __ldcg(&in.pq[own]) : in.pq[own];
+    T U = COHERENT ? __ldcg(&u[own]) : u[own], V = COHERENT ? __ldcg(&u[2 * half + own]) : u[2 * half + own];
     // FP64 V additions here: under the batch kernels' 64-register cap the
     // integer form spills (measured 1.3% slower on the batch workload, 2D)
     update_point<T, D, MODE, false, false>(in.coef, nsum_scaled(p, in.coef.beta), nsum_scaled(q, in.coef.beta),
@@ -165,6 +168,111 @@ __global__ void __launch_bounds__(kChunk, sizeof(T) == 4 ? 8 : 4) batch_pass_ker
         const int64_t t = (ch - in.first_chunk) * kChunk + threadIdx.x;
         if (t >= in.half) continue;
         batch_update<T, D, MODE, I>(in, (I)t, parity);
+    }
+}
+
+// ---- one persistent launch for a whole kgs_batch_step call ----------------
+// Every pass g = 0 .. 2 nmax of every list (both precisions, every dimension)
+// in one cooperative launch: per pass the CTAs walk the lists' chunks as one
+// index space (a chunk's list is the same for the whole CTA), the mode of each
+// instance at pass g decides its update, and a grid barrier ends the pass.
+// The barrier is bounded (kPersistWaitNs of %globaltimer): a CTA that waits
+// longer sets the error word and every CTA leaves.  Each chunk is updated by
+// the same CTA every pass; neighbour values written by other CTAs in the pass
+// before are read with L1-bypassing loads.
+struct PersistLists {
+    const void* inst[6];          // BatchInst<double> for k < 3, BatchInst<float> after; k % 3 = dim - 1
+    const int32_t* chunk_inst[6];
+    int64_t chunks[6];
+    int64_t passes;               // 2 nmax + 1
+};
+struct BatchBarrier {
+    unsigned count, gen;
+    int err, pad;
+};
+constexpr uint64_t kPersistWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t batch_clock_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool batch_grid_sync(BatchBarrier* bar, unsigned expected, unsigned& gen)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's updates before its arrival
+        if (atomicAdd(&bar->count, 1u) == expected - 1u) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const uint64_t t0 = batch_clock_ns();
+            while (atomicAdd(&bar->gen, 0u) == gen) {
+                if (atomicAdd(&bar->err, 0) != 0) break;
+                if (batch_clock_ns() - t0 > kPersistWaitNs) {
+                    atomicExch(&bar->err, 1);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();  // the other CTAs' updates before this CTA's next reads
+    }
+    ++gen;
+    __syncthreads();
+    return *(volatile int*)&bar->err == 0;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void persist_chunk(const PersistLists& pl, int k, int64_t lc, int64_t g)
+{
+    const BatchInst<T>* insts = reinterpret_cast<const BatchInst<T>*>(pl.inst[k]);
+    const BatchInst<T>& in = insts[__ldg(&pl.chunk_inst[k][lc])];
+    const int64_t n = in.nsteps;
+    if (g > 2 * n) return;
+    const int64_t t = (lc - in.first_chunk) * kChunk + threadIdx.x;
+    if (t >= in.half) return;
+    const int red = red_parity(D);
+    const int parity = (g & 1) ? (red ^ 1) : red;
+    switch (batch_mode(g, n)) {
+    case RED_BASE: batch_update<T, D, RED_BASE, int32_t, true>(in, (int32_t)t, parity); break;
+    case BLACK_FUSED: batch_update<T, D, BLACK_FUSED, int32_t, true>(in, (int32_t)t, parity); break;
+    case RED_FUSED: batch_update<T, D, RED_FUSED, int32_t, true>(in, (int32_t)t, parity); break;
+    default: batch_update<T, D, RED_ADJ, int32_t, true>(in, (int32_t)t, parity); break;
+    }
+}
+
+// expected = gridDim.x normally; the test hook sets it higher (the barrier
+// then waits for CTAs that do not exist and times out).
+__global__ void __launch_bounds__(kChunk, 4) batch_persistent_kernel(PersistLists pl, BatchBarrier* bar,
+                                                                     unsigned expected, int* err)
+{
+    int64_t prefix[7];
+    prefix[0] = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) prefix[k + 1] = prefix[k] + pl.chunks[k];
+    unsigned gen = 0;
+    for (int64_t g = 0; g < pl.passes; ++g) {
+        for (int64_t ch = blockIdx.x; ch < prefix[6]; ch += gridDim.x) {
+            int k = 0;
+            while (ch >= prefix[k + 1]) ++k;
+            const int64_t lc = ch - prefix[k];
+            switch (k) {
+            case 0: persist_chunk<double, 1>(pl, k, lc, g); break;
+            case 1: persist_chunk<double, 2>(pl, k, lc, g); break;
+            case 2: persist_chunk<double, 3>(pl, k, lc, g); break;
+            case 3: persist_chunk<float, 1>(pl, k, lc, g); break;
+            case 4: persist_chunk<float, 2>(pl, k, lc, g); break;
+            default: persist_chunk<float, 3>(pl, k, lc, g); break;
+            }
+        }
+        if (!batch_grid_sync(bar, expected, gen)) {
+            if (threadIdx.x == 0) *(volatile int*)err = 1;
+            return;
+        }
     }
 }
 
@@ -209,6 +317,15 @@ struct kgs_batch {
     int ctas_per_sm = 8;
     int ctas_list[2][3] = {{0, 0, 0}, {0, 0, 0}};  // per (precision, dimension); 0 = ctas_per_sm
     int use_graph = 1;
+    // one persistent cooperative launch per call (KGS_BATCH_OPT_PERSISTENT),
+    // its grid barrier, the error word its bounded waits set (pinned, mapped)
+    // and the test hook's phantom CTAs
+    int persistent = 0;
+    int stall = 0;
+    BatchBarrier* pbar = nullptr;
+    int* perr = nullptr;
+    bool timed_out = false;
+    bool persist_nograph = false;  // this driver refused to capture the cooperative launch
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;  // step counts the graph was captured for
     cudaEvent_t graph_ev = nullptr;  // recorded after each launch of the graph
@@ -252,6 +369,9 @@ int bcuda(kgs_batch* b, cudaError_t e, const char* what)
 int bcheck(kgs_batch* b)
 {
     if (!b) return bfail(KGS_ERR_ARG, "NULL batch handle");
+    if (b->perr && *(volatile int*)b->perr) b->timed_out = true;
+    if (b->timed_out)
+        return bfail(KGS_ERR_TIMEOUT, "batch is in error state after a device wait timed out");
     if (b->sticky)
         return bfail(KGS_ERR_CUDA, "batch is in error state after: %s",
                      cudaGetErrorString((cudaError_t)b->sticky));
@@ -452,6 +572,64 @@ int launch_list_pass(kgs_batch* b, const kgs_batch::DevList& dl, const HostList<
 }
 
 
+// The persistent launch of pass 0 .. passes-1 of every list (the lists'
+// descriptors already uploaded): the barrier zeroed on s, then one
+// cooperative launch of as many CTAs as fit on the device at once.  Returns
+// 0 or the failing call's cudaError_t (the caller decides whether it sticks).
+int launch_persistent(kgs_batch* b, const int64_t (&lchunks)[6], int64_t passes, cudaStream_t s)
+{
+    PersistLists pl;
+    for (int k = 0; k < 6; ++k) {
+        const kgs_batch::DevList& dl = b->lists[k / 3][k % 3];
+        pl.inst[k] = dl.inst;
+        pl.chunk_inst[k] = dl.chunk_inst;
+        pl.chunks[k] = lchunks[k];
+    }
+    pl.passes = passes;
+    int sms = 148, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_persistent_kernel, kChunk, 0);
+    if (e != cudaSuccess || per < 1) return (int)(e == cudaSuccess ? cudaErrorLaunchOutOfResources : e);
+    int64_t total = 0;
+    for (int64_t c : lchunks) total += c;
+    const int64_t want = b->ctas_per_sm > 0 ? std::min<int64_t>(b->ctas_per_sm, per) : per;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(total, (int64_t)sms * want));
+    const unsigned expected = grid + (unsigned)b->stall;
+    e = cudaMemsetAsync(b->pbar, 0, sizeof(BatchBarrier), s);
+    if (e != cudaSuccess) return (int)e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kChunk);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BatchBarrier* bar = b->pbar;
+    int* err = b->perr;
+    e = cudaLaunchKernelEx(&cfg, batch_persistent_kernel, pl, bar, expected, err);
+    if (e != cudaSuccess) return (int)e;
+    b->launches += 1;
+    return 0;
+}
+
+int ensure_persistent(kgs_batch* b)
+{
+    if (b->pbar) return KGS_OK;
+    cudaError_t e = cudaMalloc(&b->pbar, sizeof(BatchBarrier));
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->perr, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->pbar);
+        b->pbar = nullptr;
+        b->perr = nullptr;
+        return bfail(KGS_ERR_OOM, "persistent batch barrier: %s", cudaGetErrorString(e));
+    }
+    *(volatile int*)b->perr = 0;
+    return KGS_OK;
+}
+
 int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
 {
     HostList<double> l64[3];
@@ -486,7 +664,7 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
                                 l32[0].chunks, l32[1].chunks, l32[2].chunks};
     int nactive = 0;
     for (int k = 0; k < 6; ++k) nactive += lchunks[k] > 0;
-    if (nactive > 1 && !b->fork) {
+    if (nactive > 1 && !b->fork && !(b->persistent)) {
         cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
         for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
             e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
@@ -494,7 +672,15 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
         }
         if (e != cudaSuccess) return bcuda(b, e, "side streams");
     }
+    bool wide = false;
+    for (int d = 0; d < 3; ++d) wide = wide || l64[d].wide || l32[d].wide;
+    const bool persist = b->persistent && !wide;  // 32-bit indices only
+    if (persist && (st = ensure_persistent(b))) return st;
     auto issue = [&](cudaStream_t main) -> int {
+        if (persist) {
+            const int r = launch_persistent(b, lchunks, passes, main);
+            return r ? bcuda(b, (cudaError_t)r, "persistent batch launch") : KGS_OK;
+        }
         cudaStream_t ls[6];
         bool first = true;
         if (nactive > 1) {
@@ -530,7 +716,36 @@ int batch_run(kgs_batch* b, const int64_t* nsteps, cudaStream_t s)
         }
         return KGS_OK;
     };
-    if (!b->use_graph) return issue(s);
+    if (!b->use_graph || (persist && b->persist_nograph)) return issue(s);
+    if (persist) {
+        // one cooperative launch in a graph; if this driver refuses to capture
+        // it, launch it directly from now on (one launch per call either way)
+        drop_batch_graph(b);
+        if (!b->capture_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return bcuda(b, e, "cudaStreamCreate");
+        }
+        const int64_t before = b->launches;
+        cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        const int r = e == cudaSuccess ? launch_persistent(b, lchunks, passes, b->capture_stream) : (int)e;
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) e = cudaStreamEndCapture(b->capture_stream, &graph);
+        if (!r && e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        b->launches = before;
+        if (r || e != cudaSuccess) {
+            cudaGetLastError();
+            b->graph = nullptr;
+            b->persist_nograph = true;
+            return issue(s);
+        }
+        b->graph_launches = 1;
+        b->graph_key = key;
+        e = launch_batch_graph(b, s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch graph launch");
+        b->launches += 1;
+        return KGS_OK;
+    }
     drop_batch_graph(b);
     if (!b->capture_stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
@@ -615,6 +830,8 @@ kgs_batch_handle kgs_batch_create(int device, int64_t capacity_bytes)
               "batch arena of %lld bytes: %s", (long long)capacity_bytes, cudaGetErrorString(e));
         cudaFree(b->arena);
         cudaFree(b->scratch);
+        cudaFree(b->pbar);
+        if (b->perr) cudaFreeHost(b->perr);
         cudaFree(b->out_dev);
         if (b->out_host) cudaFreeHost(b->out_host);
         delete b;
@@ -773,6 +990,7 @@ int kgs_batch_get_state(kgs_batch_handle b, int64_t id, double* P, double* Q, do
         cudaFreeAsync(stage, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize");
+        return bcheck(b);  // a persistent launch before it may have timed out
     }
     return KGS_OK;
 }
@@ -833,6 +1051,7 @@ int kgs_batch_invariants(kgs_batch_handle b, int64_t id, double* out3, void* str
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bcuda(b, e, "invariants readback");
+    if ((st = bcheck(b))) return st;  // a persistent launch before it may have timed out
     for (int k = 0; k < 3; ++k) out3[k] = b->out_host[k];
     return KGS_OK;
 }
@@ -864,6 +1083,16 @@ int kgs_batch_set_option(kgs_batch_handle b, int option, int64_t value)
     case KGS_BATCH_OPT_GRAPH:
         if (value < 0 || value > 1) return bfail(KGS_ERR_ARG, "graph option takes 0 or 1");
         b->use_graph = (int)value;
+        drop_batch_graph(b);
+        return KGS_OK;
+    case KGS_BATCH_OPT_PERSISTENT:
+        if (value < 0 || value > 1) return bfail(KGS_ERR_ARG, "persistent option takes 0 or 1");
+        b->persistent = (int)value;
+        drop_batch_graph(b);
+        return KGS_OK;
+    case KGS_BATCH_OPT_TEST_STALL:
+        if (value < 0 || value > 1024) return bfail(KGS_ERR_ARG, "stall test hook takes 0 to 1024");
+        b->stall = (int)value;
         drop_batch_graph(b);
         return KGS_OK;
     default:

@@ -332,6 +332,8 @@ def probe_psi_weight(r, stream=None):
 
 KGS_BATCH_OPT_CTAS_PER_SM = 1
 KGS_BATCH_OPT_GRAPH = 2
+KGS_BATCH_OPT_PERSISTENT = 3
+KGS_BATCH_OPT_TEST_STALL = 4
 KGS_BATCH_OPT_CTAS_LIST = 16  # + 3 p + (dim - 1), p = 0 FP64 / 1 FP32
 
 

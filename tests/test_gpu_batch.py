@@ -130,3 +130,61 @@ def test_tuned_batch_lists_are_bitwise_the_defaults():
     for got, want in zip(results[1], results[0]):
         for x, y in zip(got, want):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_persistent_launch_is_bitwise_the_per_pass_launches(graph):
+    """KGS_BATCH_OPT_PERSISTENT: a step call is one cooperative launch running
+    every colour pass of every instance (both precisions, 1D/2D/3D, per-instance
+    step counts, a 4-point grid) with a grid barrier between passes; every
+    instance's state is bitwise that of the per-pass launches, on repeated
+    calls (graph replay) and after a change of step counts (a new graph)."""
+    from paper_2502_09537_b300.solver import KGS_BATCH_OPT_PERSISTENT
+    states = [random_state(p, 700 + k, 0.6) for k, (p, _) in enumerate(MIX)]
+    plans = [[5, 0, 17, 1, 9, 17, 3], [4, 4, 4, 4, 4, 4, 4]]
+    results = []
+    for persistent in (0, 1):
+        with Batch(1 << 28) as b:
+            b.set_option(KGS_BATCH_OPT_GRAPH, graph)
+            b.set_option(KGS_BATCH_OPT_PERSISTENT, persistent)
+            ids = [b.add(p, prec) for p, prec in MIX]
+            for i, st in zip(ids, states):
+                b.set_state(i, *[a.copy() for a in st])
+            l0 = b.launch_count
+            b.step_each(plans[0])
+            b.step_each(plans[0])
+            b.step_each(plans[1])
+            if persistent:
+                assert b.launch_count - l0 == 3   # one launch per call
+            results.append([b.get_state(i) for i in ids])
+    for got, want in zip(results[1], results[0]):
+        for x, y in zip(got, want):
+            assert np.array_equal(x, y)
+
+
+def test_persistent_launch_barrier_timeout_is_reported():
+    """The test hook makes the persistent launch's grid barrier wait for CTAs
+    that do not exist: the wait ends after its 2 s limit, every CTA leaves,
+    the batch reports KGS_ERR_TIMEOUT from its next call on, and a new batch
+    steps correctly."""
+    from paper_2502_09537_b300.solver import (KGS_BATCH_OPT_PERSISTENT, KGS_BATCH_OPT_TEST_STALL,
+                                              KGS_ERR_TIMEOUT)
+    p, prec = MIX[1]
+    st = random_state(p, 77, 0.5)
+    with Batch(1 << 26) as b:
+        b.set_option(KGS_BATCH_OPT_PERSISTENT, 1)
+        b.set_option(KGS_BATCH_OPT_TEST_STALL, 1)
+        i = b.add(p, prec)
+        b.set_state(i, *[a.copy() for a in st])
+        b.step(3)
+        with pytest.raises(KGSError) as ei:
+            b.invariants(i)
+        assert ei.value.status == KGS_ERR_TIMEOUT
+    want, _ = solo(p, prec, st, 3)
+    with Batch(1 << 26) as b:
+        b.set_option(KGS_BATCH_OPT_PERSISTENT, 1)
+        i = b.add(p, prec)
+        b.set_state(i, *[a.copy() for a in st])
+        b.step(3)
+        for x, y in zip(b.get_state(i), want):
+            assert np.array_equal(x, y)
