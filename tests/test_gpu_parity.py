@@ -364,11 +364,18 @@ def test_full_size_3d_first_step_and_energy(orc):
 
 
 def test_fp32_state_close_to_fp64_oracle(orc):
-    """Float32 state and arithmetic: not bit-comparable; its max-norm error
-    against the FP64 oracle and its energy drift are reported and bounded by
-    what float32 rounding (6e-8 per operation) allows over the run."""
+    """Float32 state and arithmetic on the 1D configuration (2000 steps): not
+    bit-comparable; its max-norm error against the FP64 oracle and its energy
+    drift are bounded by what float32 rounding allows over the run,
+    (1 + 4 n) u max(A, 1) with u = 2^-24 and A the run's amplification of a
+    float32-sized perturbation of its initial state (measured on the oracle;
+    the derivation is the one of the 3D configuration's FP32 tests)."""
     w = inputs.soliton_1d(512, 2000)
     ref = run_oracle(orc, w.prob, w.state, w.nsteps)
+    pert = run_oracle(orc, w.prob, tuple(np.asarray(a, dtype=np.float32).astype(np.float64)
+                                         for a in w.state), w.nsteps)
+    u = 2.0 ** -24
+    A = max(1.0, rel_err(pert, ref) / u)
     with Solver.from_problem(w.prob, KGS_FP32) as s:
         s.set_state(*copy_state(w.state))
         E0, S0, _ = s.invariants()
@@ -377,9 +384,10 @@ def test_fp32_state_close_to_fp64_oracle(orc):
         got = s.get_state()
     err = rel_err(got, ref)
     drift = abs(E1 - E0) / max(S0, S1)
-    print(f"fp32 1D soliton: max-norm rel error {err:.2e}, energy drift {drift:.2e}")
-    assert err < 1e-3
-    assert drift < 1e-4
+    bound = (1 + 4 * w.nsteps) * u * A
+    print(f"fp32 1D soliton: max-norm rel error {err:.2e}, energy drift {drift:.2e}, bound {bound:.2e} (A {A:.2f})")
+    assert err <= bound
+    assert drift <= bound
 
 
 TILE_CASES = [
