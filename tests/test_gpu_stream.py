@@ -47,6 +47,19 @@ def test_streamed_planes_are_bitwise_the_pass_kernel(N, splits, chunk):
     assert inv_got == inv_want
 
 
+def test_streamed_planes_one_row_last_tile():
+    """N = 320 = 11 x 29 + 1: the last row of tiles holds a single row (the
+    ring rows are its neighbours on both sides; most of its box is
+    zero-filled beyond the grid)."""
+    prob = Problem(3, 320, 20.0, 1.1, 0.9, 1.2, 0.8, 5e-4 * (512 / 320) ** 2)
+    st = random_state(prob, 2502_09537 + 320, 0.5)
+    want, inv_want = run(prob, st, [3], 1)
+    got, inv_got = run(prob, st, [1, 2], STREAM)
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+    assert inv_got == inv_want
+
+
 def test_streamed_planes_are_the_default_for_fp32_3d():
     """KGS_OPT_KERNEL 0 (auto) takes the streamed planes for a float32 3D grid
     it fits: bitwise kernel 7's state and launch count."""
