@@ -81,7 +81,7 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 NCU_TRAFFIC = {("2d", "fp64", "pass"): 117.52e6 + 25.74e6,
                ("3d", "fp64", "pass"): 3.7645e9 + 2.1086e9,
                ("3d", "fp32", "pass"): 1.8822e9 + 1.0321e9,
-               ("3d", "fp32", "stream"): 2.2918e9 + 2.1541e9}
+               ("3d", "fp32", "stream"): 2.2622e9 + 2.1531e9}
 
 
 # Issue-slot view of the float64 colour passes: the fraction of peak each

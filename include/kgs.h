@@ -135,7 +135,9 @@ extern "C" {
 #define KGS_OPT_STREAM_CHUNK 16 /* streamed-plane kernel (7): C > 0: work items of C axis-0 planes
                                    of a tile, taken round-robin chunk by chunk, so that neighbouring
                                    tiles stream the same planes together (their shared halo rows
-                                   then come from L2); 0 (default) = 64; -1: each CTA takes a
+                                   then come from L2); 0 (default) = the fewest chunks per tile
+                                   column, at least two, that fill 95% of the rounds of CTAs over
+                                   the SMs (256 planes at N = 512 on 148 SMs); -1: each CTA takes a
                                    contiguous share of the (tile, plane) sequence instead.  Bitwise
                                    the same state. */
 #define KGS_OPT_STREAM_PREFETCH 17 /* streamed-plane kernel (7): planes beyond its shared-memory

@@ -728,9 +728,11 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
             int cs = 0;
             for (int64_t k = 0; k < nsteps; ++k) {
                 const int mode = k == nsteps - 1 ? RED_ADJ : RED_FUSED;
-                // 64-plane chunks by default (measured at 512^3: 0.724 of HBM against
-                // 0.699 for contiguous shares and 0.698 for 32-plane chunks)
-                const int chunk = h->opt_stream_chunk == 0 ? 64 : (h->opt_stream_chunk < 0 ? 0 : h->opt_stream_chunk);
+                // chunk planes: the caller's, or the grid's default (stream_auto_chunk)
+                int sms = 148;
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+                const int chunk = h->opt_stream_chunk == 0 ? stream_auto_chunk(h->N, sms)
+                                                          : (h->opt_stream_chunk < 0 ? 0 : h->opt_stream_chunk);
                 const int pf = h->opt_stream_prefetch < 0 ? 2 : h->opt_stream_prefetch;
                 if (launch_stream(h->smap[cs], h->sbuf[cs ^ 1], h->N, h->cf, mode, h->werr, h->opt_stall, chunk, pf,
                                   s) < 0)

@@ -114,6 +114,8 @@ int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<
 // returns 1 (kernels launched) or -1 if a launch failed.
 bool stream_applies(int dim, int64_t N, int precision);
 size_t stream_buffer_bytes(int64_t N);
+// The default chunk of planes per work item for a grid on `sms` SMs.
+int stream_auto_chunk(int64_t N, int sms);
 int stream_make_map(void* buf, int64_t N, void* map_out);
 int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, int red_mode, int* err, int stall,
                   int chunk, int prefetch, cudaStream_t s);

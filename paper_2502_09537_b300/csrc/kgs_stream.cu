@@ -14,8 +14,9 @@
 //
 // Work: a tile is 29 x 64 points of the other two axes (29 rows along axis 1,
 // 32 points of each colour along the last axis; the last tile of a grid has
-// the rows that are left).  One CTA per SM takes work items of 64 consecutive
-// axis-0 planes of a tile, round-robin in chunk-major order, so that CTAs on
+// the rows that are left).  One CTA per SM takes work items of consecutive
+// axis-0 planes of a tile (chunks: stream_auto_chunk, 256 planes at N = 512),
+// round-robin in chunk-major order, so that CTAs on
 // neighbouring tiles stream the same planes at about the same time and the
 // halo rows they share come from L2 for the second.  For an item's planes
 // [x0, x0 + L) it stages planes x0-2 .. x0+L+1 (mod N), updates black on
@@ -386,6 +387,29 @@ unsigned conv_grid(int64_t n)
 bool stream_applies(int dim, int64_t N, int precision)
 {
     return dim == 3 && precision == 32 && N >= 64 && N <= 1024 && N % 64 == 0;
+}
+
+int stream_auto_chunk(int64_t N, int sms)
+{
+    // the fewest chunks per tile column (at least two: a column alone measured
+    // slower) whose items fill at least 95% of the rounds of `sms` CTAs, else
+    // the best filling; measured at 512^3 (144 tiles): 256-plane chunks 0.750
+    // of HBM, 171: 0.746, 128: 0.744, 512: 0.739, 64: 0.730
+    const int64_t ntiles = ((N + kTy - 1) / kTy) * (N / 2 / kTh);
+    int best = (int)N;
+    double best_fill = 0.0;
+    for (int64_t nc = 2; nc <= N / 16; ++nc) {
+        const int64_t chunk = (N + nc - 1) / nc;
+        const int64_t items = ntiles * ((N + chunk - 1) / chunk);
+        const int64_t rounds = (items + sms - 1) / sms;
+        const double fill = (double)items / (double)(rounds * sms);
+        if (fill > best_fill + 1e-9) {
+            best_fill = fill;
+            best = (int)chunk;
+        }
+        if (fill >= 0.95) return (int)chunk;
+    }
+    return best;
 }
 
 size_t stream_buffer_bytes(int64_t N)
