@@ -97,10 +97,13 @@ NCU_PIPES = {("2d", "fp64", "pass"): {"fp64": 0.874, "alu": 0.746, "fma": 0.129,
 def kernel_name(args, precision=None):
     """The dominant kernel of a solve: what KGS_OPT_KERNEL selects (0 = the
     library's automatic choice, which streams float32 3D grids whose N is a
-    multiple of 64, up to 1024, and makes one launch per pass otherwise)."""
+    multiple of 64, up to 1024, and makes one launch per pass otherwise;
+    "stream2": two steps per launch, KGS_OPT_KERNEL 8)."""
     precision = precision or args.precision
     n = args.grid_n or {"1d": 512, "2d": 2048, "3d": 512}.get(args.workload, 0)
     streams = args.workload == "3d" and precision == "fp32" and n % 64 == 0 and 64 <= n <= 1024
+    if args.kernel == 8:
+        return "stream2" if streams else "pass"
     if args.kernel == 7 or (args.kernel == 0 and streams):
         return "stream" if streams else "pass"
     return "pass" if args.kernel in (0, 1) else None
@@ -124,10 +127,16 @@ def traffic_of(args, precision=None):
 FP64_PEAK_TFLOPS = 2 * 2 * 148 * 2.032e9 / 1e12
 
 
-def bytes_per_point_update(elem: int) -> int:
+def bytes_per_point_update(elem: int, depth: int = 1) -> float:
     """Algorithmic HBM bytes of one point-update: read and write the four
-    fields once (the two colour passes of a step each touch their own half)."""
-    return 2 * 4 * elem
+    fields once per launch (the two colour passes of a step each touch their
+    own half), over the `depth` steps a launch applies."""
+    return 2 * 4 * elem / depth
+
+
+def temporal_depth(args, precision=None) -> int:
+    """Steps per launch of the dominant kernel."""
+    return 2 if kernel_name(args, precision) == "stream2" else 1
 
 
 def make_workload(name: str, n: int = 0):
@@ -609,14 +618,15 @@ def solo_leg(args, work, precision_name, init_dev, flush, local, dist, world, st
                                      note="fraction of each pipe's peak issue rate over active cycles, "
                                           "ncu capture of these launches")
     else:
-        achieved = upd_per_launch * bytes_per_point_update(elem) / (pass_ms * 1e-3) / 1e9
+        depth = temporal_depth(args, precision_name)
+        achieved = upd_per_launch * bytes_per_point_update(elem, depth) / (pass_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": traffic_of(args, precision_name),
                 "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                                 else "fallback 6.4 TB/s (of fallback)"),
-                "bytes_per_point_update": bytes_per_point_update(elem)}
+                "bytes_per_point_update": bytes_per_point_update(elem, depth), "temporal_depth": depth}
     leg = {
         "value": value, "ms_per_step": total_ms / steps,
         "ms_per_step_median": float(np.median(iter_ms)), "steps": steps, "warmup": warmup,

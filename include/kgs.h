@@ -85,9 +85,14 @@ extern "C" {
                                every plane of a 29 x 64 tile staged by a TMA tensor load
                                (float32 state, dim 3, N a multiple of 64 up to 1024; allocates
                                two packed copies of the state, about 2.2 GB each at N = 512, on
-                               first use; other grids run the plain passes).  Auto picks 2 for
-                               grids that fit one CTA's shared memory, 7 where it applies, 1
-                               otherwise.  All give bitwise the same state. */
+                               first use; other grids run the plain passes), 8 streamed planes,
+                               two steps per launch: a step pair's four colour passes chained
+                               plane by plane in one launch over 23 x 64 tiles staged with a
+                               four-row halo (temporal depth 2: one read and one write of the
+                               state per two steps; an odd step count ends with one launch of
+                               7; same grids and buffers as 7).  Auto picks 2 for grids that fit
+                               one CTA's shared memory, 7 where it applies, 1 otherwise.  All
+                               give bitwise the same state. */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
 #define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
 #define KGS_OPT_PPT      4  /* points of one colour per thread in those kernels: 1 only (2 was
@@ -132,15 +137,15 @@ extern "C" {
                                    for the one before, so a pass's launch overlaps the previous
                                    pass's tail (+0.3% on the 2D FP64 workload); 0 plain launches.
                                    Bitwise the same state either way. */
-#define KGS_OPT_STREAM_CHUNK 16 /* streamed-plane kernel (7): C > 0: work items of C axis-0 planes
+#define KGS_OPT_STREAM_CHUNK 16 /* streamed-plane kernels (7, 8): C > 0: work items of C axis-0 planes
                                    of a tile, taken round-robin chunk by chunk, so that neighbouring
                                    tiles stream the same planes together (their shared halo rows
                                    then come from L2); 0 (default) = the fewest chunks per tile
                                    column, at least two, that fill 95% of the rounds of CTAs over
-                                   the SMs (256 planes at N = 512 on 148 SMs); -1: each CTA takes a
-                                   contiguous share of the (tile, plane) sequence instead.  Bitwise
-                                   the same state. */
-#define KGS_OPT_STREAM_PREFETCH 17 /* streamed-plane kernel (7): planes beyond its shared-memory
+                                   the SMs (256 planes at N = 512 on 148 SMs for 7, 128 for 8);
+                                   -1: each CTA takes a contiguous share of the (tile, plane)
+                                   sequence instead.  Bitwise the same state. */
+#define KGS_OPT_STREAM_PREFETCH 17 /* streamed-plane kernels (7, 8): planes beyond its shared-memory
                                    loads that a CTA also asks L2 to fetch ahead (TMA prefetch),
                                    0 .. 16; default 2.  Bitwise the same state. */
 #define KGS_OPT_SLAB_PLANES 10  /* slab and wave kernels: axis-0 planes per slab, 1 .. N (the

@@ -68,6 +68,20 @@ int kgs_probe_psi_weight(int64_t n, const double* r_host, double* w_host, void* 
  * NULL flags or -4 if a CUDA call failed. */
 int kgs_debug_bounds(uint32_t* flags);
 
+/* The side list of the float32 3D two-steps-per-launch kernel
+ * (KGS_OPT_KERNEL 8) for an N^3 grid, as the host builds it (no device
+ * needed): the points beyond a tile's 32 colour columns that its first three
+ * colour passes update, per tile kind (0: 23-row tiles, 1: the grid's last,
+ * shorter row of tiles) and plane parity q.  out receives 2 x 2 x 96 entries
+ * (kind-major, then q, then the list index), each staged row | staged column
+ * << 5 | (passes - 1) << 11 | 0x8000 (staged row = tile row + 4, staged
+ * column = colour column + 2) or 0 past the list's end, then the 2 x 2 list
+ * lengths.  cap: uint16 entries at out.  Returns the entries written (388),
+ * -1 for a bad argument (N not even or < 4, out NULL, cap < 388) or -2 if
+ * the grid's regions break the kernel's thread layout (then the kernel is
+ * not used for it). */
+int kgs_stream2_side_list(int64_t N, uint16_t* out, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,11 @@ struct kgs_solver {
     // and their TMA tensor maps (CUtensorMap storage)
     void* sbuf[2] = {nullptr, nullptr};
     alignas(64) unsigned char smap[2][128] = {};
+    // two steps per launch (KGS_OPT_KERNEL 8): the staged box's tensor maps
+    // and the grid's side list (sside_ok: stream2_prepare succeeded)
+    alignas(64) unsigned char smap2[2][128] = {};
+    alignas(16) unsigned char sside[kStream2SideBytes] = {};
+    bool sside_ok = false;
     int opt_stream_chunk = 0;  // KGS_OPT_STREAM_CHUNK
     // device bytes this handle may allocate (KGS_DEVICE_BUDGET at creation; 0 =
     // no limit) and the bytes it holds
@@ -202,7 +207,9 @@ Grid grid_of(const kgs_solver* h)
     return g;
 }
 
-enum KernelChoice { K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5, K_WAVE = 6, K_STREAM = 7 };
+enum KernelChoice {
+    K_PASS = 1, K_SMEM = 2, K_TILE = 3, K_PERSIST = 4, K_SLAB = 5, K_WAVE = 6, K_STREAM = 7, K_STREAM2 = 8
+};
 
 // Default tile shape per dimension and precision (measured on B300; the batch
 // autotuner can override it per handle).
@@ -222,7 +229,7 @@ TileParams default_tile(int dim, int precision)
 int kernel_choice(const kgs_solver* h)
 {
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
-    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_STREAM) return h->opt_kernel;
+    if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_STREAM2) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
     // Float32 3D grids the streamed-plane kernel takes: a step's two passes in
     // one read and one write of the state (measured at 512^3: 1.257e11
@@ -272,13 +279,14 @@ int ensure_stream(kgs_solver* h)
                     "streamed-plane buffers (2 x %zu bytes): %s", bytes, cudaGetErrorString(e));
     }
     for (int b = 0; b < 2; ++b) {
-        if (stream_make_map(h->sbuf[b], h->N, h->smap[b])) {
+        if (stream_make_map(h->sbuf[b], h->N, 1, h->smap[b]) || stream_make_map(h->sbuf[b], h->N, 2, h->smap2[b])) {
             hfree(h, h->sbuf[0], bytes);
             hfree(h, h->sbuf[1], bytes);
             h->sbuf[0] = h->sbuf[1] = nullptr;
             return fail(KGS_ERR_CUDA, "TMA tensor map of the streamed-plane buffers");
         }
     }
+    h->sside_ok = stream2_prepare(h->N, h->sside) == 0;
     return KGS_OK;
 }
 
@@ -717,31 +725,42 @@ int step_impl(kgs_solver* h, int64_t nsteps, cudaStream_t s)
         return KGS_OK;
     }
     if constexpr (sizeof(T) == 4) {
-        if (kc == K_STREAM && stream_applies(h->dim, h->N, h->precision)) {
-            // R_base on the handle's layout, then every (black, red) pair streamed
-            // on the packed copies (the last with the adjoint red half), back
+        if ((kc == K_STREAM || kc == K_STREAM2) && stream_applies(h->dim, h->N, h->precision)) {
+            // R_base on the handle's layout, then the steps streamed on the packed
+            // copies -- two per launch (KGS_OPT_KERNEL 8) or one, the last with
+            // the adjoint red half -- and back
             int st = ensure_stream(h);
             if (st) return st;
             if (pass<T>(h, RED_BASE, s)) return cuda_fail(h, cudaGetLastError(), "colour pass launch");
             if (launch_to_packed(h->pqb[h->cur], h->uvb[h->cur], h->sbuf[0], h->N, s) < 0)
                 return cuda_fail(h, cudaGetLastError(), "layout conversion");
+            int sms = 148;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+            const bool two = kc == K_STREAM2 && h->sside_ok;
+            // chunk planes: the caller's, or the grid's default
+            const int chunk1 = h->opt_stream_chunk == 0 ? stream_auto_chunk(h->N, sms)
+                                                        : (h->opt_stream_chunk < 0 ? 0 : h->opt_stream_chunk);
+            const int chunk2 = h->opt_stream_chunk == 0 ? stream2_auto_chunk(h->N, sms)
+                                                        : (h->opt_stream_chunk < 0 ? 0 : h->opt_stream_chunk);
+            // L2 prefetch distance: the caller's, or 2 planes (one step per launch at 512^3: 1 / 2 / 4
+            // planes 0.733 / 0.732 / 0.730 of HBM; two steps: 2 and 6 planes alike, 1.714 / 1.715 ms)
+            const int pf = h->opt_stream_prefetch < 0 ? 2 : h->opt_stream_prefetch;
             int cs = 0;
-            for (int64_t k = 0; k < nsteps; ++k) {
-                const int mode = k == nsteps - 1 ? RED_ADJ : RED_FUSED;
-                // chunk planes: the caller's, or the grid's default (stream_auto_chunk)
-                int sms = 148;
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-                const int chunk = h->opt_stream_chunk == 0 ? stream_auto_chunk(h->N, sms)
-                                                          : (h->opt_stream_chunk < 0 ? 0 : h->opt_stream_chunk);
-                const int pf = h->opt_stream_prefetch < 0 ? 2 : h->opt_stream_prefetch;
-                if (launch_stream(h->smap[cs], h->sbuf[cs ^ 1], h->N, h->cf, mode, h->werr, h->opt_stall, chunk, pf,
-                                  s) < 0)
-                    return cuda_fail(h, cudaGetLastError(), "streamed-plane launch");
+            int64_t nl = 0;
+            for (int64_t k = 0; k < nsteps; ++nl) {
+                const int take = two && nsteps - k >= 2 ? 2 : 1;
+                const int mode = k + take == nsteps ? RED_ADJ : RED_FUSED;
+                const int r = take == 2 ? launch_stream2(h->smap2[cs], h->sside, h->sbuf[cs ^ 1], h->N, h->cf, mode,
+                                                         h->werr, h->opt_stall, chunk2, pf, s)
+                                        : launch_stream(h->smap[cs], h->sbuf[cs ^ 1], h->N, h->cf, mode, h->werr,
+                                                        h->opt_stall, chunk1, pf, s);
+                if (r < 0) return cuda_fail(h, cudaGetLastError(), "streamed-plane launch");
                 cs ^= 1;
+                k += take;
             }
             if (launch_from_packed(h->sbuf[cs], h->pqb[h->cur], h->uvb[h->cur], h->N, s) < 0)
                 return cuda_fail(h, cudaGetLastError(), "layout conversion");
-            h->launches += nsteps + 2;  // (the R_base pass counted itself)
+            h->launches += nl + 2;  // (the R_base pass counted itself)
             return KGS_OK;
         }
     }
@@ -1153,7 +1172,7 @@ int kgs_set_option(kgs_handle h, int option, int64_t value)
     if (st) return st;
     switch (option) {
     case KGS_OPT_KERNEL:
-        if (value < 0 || value > 7) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 7");
+        if (value < 0 || value > 8) return fail(KGS_ERR_ARG, "KGS_OPT_KERNEL takes 0 to 8");
         if (value == 5 && h->dim < 2) return fail(KGS_ERR_ARG, "the slab kernel needs dim 2 or 3");
         if (value == 6 && h->dim < 2) return fail(KGS_ERR_ARG, "the wave kernel needs dim 2 or 3");
         if (value == 2 && h->M > smem_resident_max_points(h->precision == 64 ? 8 : 4))

@@ -98,7 +98,7 @@ int launch_tile(const Grid& g, TileParams tp, const vec2_t<T>* pq, const vec2_t<
 
 // Streamed planes (kgs_stream.cu): float32 3D step pairs, a step's black and
 // red passes in one launch walking axis 0, planes staged by TMA tensor loads,
-// on a private packed layout (per colour and plane, (N + 4) rows of N/2 + 4
+// on a private packed layout (per colour and plane, (N + 8) rows of N/2 + 4
 // float4 (P, Q, U, V), with ghost copies of the periodic neighbours).
 // stream_applies: whether a grid qualifies; stream_buffer_bytes: one packed
 // copy of the state; stream_make_map: the TMA tensor map (a 64-byte aligned,
@@ -116,9 +116,20 @@ bool stream_applies(int dim, int64_t N, int precision);
 size_t stream_buffer_bytes(int64_t N);
 // The default chunk of planes per work item for a grid on `sms` SMs.
 int stream_auto_chunk(int64_t N, int sms);
-int stream_make_map(void* buf, int64_t N, void* map_out);
+// steps: 1 for launch_stream's staged box, 2 for launch_stream2's.
+int stream_make_map(void* buf, int64_t N, int steps, void* map_out);
 int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, int red_mode, int* err, int stall,
                   int chunk, int prefetch, cudaStream_t s);
+// Two steps per launch (temporal depth 2) on the same packed buffers:
+// stream2_prepare writes the per-grid list of points beyond the tiles'
+// columns (kStream2SideBytes at side_out; -1 if the grid's tiles do not fit
+// the kernel's thread layout); launch_stream2 applies (BLACK_FUSED,
+// RED_FUSED, BLACK_FUSED, red_mode), arguments otherwise as launch_stream's.
+constexpr size_t kStream2SideBytes = 1024;
+int stream2_auto_chunk(int64_t N, int sms);
+int stream2_prepare(int64_t N, void* side_out);
+int launch_stream2(const void* map, const void* side, void* dst, int64_t N, const Coef<float>& c, int red_mode,
+                   int* err, int stall, int chunk, int prefetch, cudaStream_t s);
 int launch_to_packed(const void* pq, const void* uv, void* out, int64_t N, cudaStream_t s);
 int launch_from_packed(const void* in, void* pq, void* uv, int64_t N, cudaStream_t s);
 

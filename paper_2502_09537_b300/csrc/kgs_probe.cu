@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "kgs_internal.h"
 
 namespace {
@@ -160,4 +162,14 @@ extern "C" int kgs_debug_bounds(uint32_t* flags)
 #else
     return 0;
 #endif
+}
+
+extern "C" int kgs_stream2_side_list(int64_t N, uint16_t* out, int64_t cap)
+{
+    constexpr int64_t kEntries = 2 * 2 * 96 + 4;
+    if (N < 4 || N % 2 || !out || cap < kEntries) return -1;
+    alignas(16) unsigned char buf[kgs::kStream2SideBytes];
+    if (kgs::stream2_prepare(N, buf)) return -2;
+    memcpy(out, buf, kEntries * sizeof(uint16_t));
+    return (int)kEntries;
 }

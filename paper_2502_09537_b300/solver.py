@@ -88,6 +88,7 @@ SIGNATURES = {
     "kgs_probe_nsum": (ctypes.c_int, [ctypes.c_int, _c_int64, _vp, _c_dbl, _vp, _vp, _vp, _vp]),
     "kgs_probe_psi_weight": (ctypes.c_int, [_c_int64, _vp, _vp, _vp]),
     "kgs_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
+    "kgs_stream2_side_list": (ctypes.c_int, [_c_int64, _vp, _c_int64]),
 }
 
 _lib = None
@@ -122,6 +123,17 @@ def debug_bounds():
     if r < 0:
         raise KGSError(r, "kgs_debug_bounds failed")
     return bool(r), int(f.value)
+
+
+def stream2_side_list(N: int):
+    """The two-step kernel's side list for an N^3 grid (kgs_stream2_side_list):
+    entries (2, 2, 96) uint16 by tile kind and plane parity, and the list
+    lengths (2, 2)."""
+    buf = np.zeros(388, dtype=np.uint16)
+    r = load_library().kgs_stream2_side_list(N, buf.ctypes.data, buf.size)
+    if r < 0:
+        raise KGSError(r, "kgs_stream2_side_list failed")
+    return buf[:384].reshape(2, 2, 96).astype(np.int64), buf[384:].reshape(2, 2).astype(np.int64)
 
 
 def last_error() -> str:

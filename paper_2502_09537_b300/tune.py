@@ -56,8 +56,10 @@ def candidates(prob, precision: int) -> List[Options]:
     if prob.dim >= 2:
         out.append({KGS_OPT_KERNEL: 5})  # colour passes pipelined in L2-sized axis-0 slabs
     if prob.dim == 3 and precision != KGS_FP64 and prob.N % 64 == 0 and 64 <= prob.N <= 1024:
-        # streamed planes: a step's two passes in one launch, in chunk orders
+        # streamed planes: a step's two passes in one launch, in chunk orders,
+        # and a step pair's four passes in one launch
         out += [{KGS_OPT_KERNEL: 7, KGS_OPT_STREAM_CHUNK: ch} for ch in (0, 32, 128, -1)]
+        out += [{KGS_OPT_KERNEL: 8, KGS_OPT_STREAM_CHUNK: ch} for ch in (0, -1)]
     if prob.points <= SMEM_BYTES // (4 * elem):
         out.append({KGS_OPT_KERNEL: 2})
     if prob.dim == 2:

@@ -29,7 +29,7 @@ checking, flags0 = solver.debug_bounds()
 cases = []
 for dim, N in ((1, 4), (1, 6), (1, 130), (2, 4), (2, 6), (2, 66), (3, 4), (3, 6), (3, 18), (3, 64)):
     for prec in (KGS_FP64, KGS_FP32):
-        for kernel in (1, 4, 5, 7):
+        for kernel in (1, 4, 5, 7, 8):
             if kernel == 5 and dim < 2:
                 continue
             prob = Problem(dim, N, 5.0, 1.0, 0.9, 1.1, 1.2, 0.01)
