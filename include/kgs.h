@@ -66,6 +66,7 @@ extern "C" {
 /* memory kind of caller buffers */
 #define KGS_HOST   0
 #define KGS_DEVICE 1
+#define KGS_HOST_ASYNC 2  /* host memory, queued on the stream without waiting (see kgs_set_state) */
 
 /* state precision (kgs_create_ex) */
 #define KGS_FP64 64  /* state and arithmetic in float64 */
@@ -177,13 +178,20 @@ kgs_handle kgs_create_ex(int dim, int64_t N, double L, double kappa1, double kap
  * host memory (where = KGS_HOST; pinned or pageable; returns after the copy)
  * or device memory of the handle's device (where = KGS_DEVICE; asynchronous on
  * stream; the buffers must stay valid until the stream reaches this point).
- * FP32 handles round each value to float32. */
+ * where = KGS_HOST_ASYNC: host memory, copied asynchronously on stream like
+ * device memory (the buffers must stay valid and unchanged until the stream
+ * reaches this point; pinned memory lets the copies overlap other streams'
+ * work, pageable memory makes them synchronous).  The handle's one staging
+ * buffer carries every host copy in and out, so host copies of one handle
+ * must be ordered with each other and with its kgs_step calls (one stream,
+ * or events).  FP32 handles round each value to float32. */
 int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* U,
                   const double* V, int where, void* stream);
 
 /* Copy the state out as four float64 arrays (FP32 state is widened exactly).
- * Host buffers are filled when the call returns; device buffers are written
- * asynchronously on stream. */
+ * Host buffers are filled when the call returns; device buffers (and host
+ * buffers with where = KGS_HOST_ASYNC) are written asynchronously on stream,
+ * with the ordering rules of kgs_set_state. */
 int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V,
                   int where, void* stream);
 
@@ -344,7 +352,8 @@ int kgs_batch_remove(kgs_batch_handle b, int64_t id);
 int64_t kgs_batch_free_bytes(kgs_batch_handle b);
 
 /* State in / out of one instance; arguments and behaviour as kgs_set_state /
- * kgs_get_state (host buffers use a temporary device staging buffer). */
+ * kgs_get_state with KGS_HOST or KGS_DEVICE (host buffers use a temporary
+ * device staging buffer; KGS_HOST_ASYNC is refused with KGS_ERR_ARG). */
 int kgs_batch_set_state(kgs_batch_handle b, int64_t id, const double* P, const double* Q,
                         const double* U, const double* V, int where, void* stream);
 int kgs_batch_get_state(kgs_batch_handle b, int64_t id, double* P, double* Q, double* U,

@@ -907,14 +907,16 @@ int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* 
     int st = check_handle(h);
     if (st) return st;
     if (!P || !Q || !U || !V) return fail(KGS_ERR_ARG, "NULL state pointer");
-    if (where != KGS_HOST && where != KGS_DEVICE) return fail(KGS_ERR_ARG, "where must be KGS_HOST or KGS_DEVICE");
+    if (where != KGS_HOST && where != KGS_DEVICE && where != KGS_HOST_ASYNC)
+        return fail(KGS_ERR_ARG, "where must be KGS_HOST, KGS_DEVICE or KGS_HOST_ASYNC");
     DeviceGuard guard(h->device);
     if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     const double* src[4] = {P, Q, U, V};
+    const bool host = where != KGS_DEVICE;
     for (int f = 0; f < 4; ++f) {
         const double* d = src[f];
-        if (where == KGS_HOST) {
+        if (host) {
             cudaError_t e = cudaMemcpyAsync(h->stage, src[f], (size_t)h->M * sizeof(double),
                                             cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "state upload");
@@ -927,7 +929,7 @@ int kgs_set_state(kgs_handle h, const double* P, const double* Q, const double* 
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "pack launch");
         h->launches += n;
     }
-    if (where == KGS_HOST) {
+    if (where == KGS_HOST) {  // (KGS_HOST_ASYNC: the caller waits for the stream)
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     }
@@ -942,20 +944,22 @@ int kgs_get_state(kgs_handle h, double* P, double* Q, double* U, double* V, int 
     if (st) return st;
     if (!h->state_set) return fail(KGS_ERR_STATE, "no state set");
     if (!P || !Q || !U || !V) return fail(KGS_ERR_ARG, "NULL state pointer");
-    if (where != KGS_HOST && where != KGS_DEVICE) return fail(KGS_ERR_ARG, "where must be KGS_HOST or KGS_DEVICE");
+    if (where != KGS_HOST && where != KGS_DEVICE && where != KGS_HOST_ASYNC)
+        return fail(KGS_ERR_ARG, "where must be KGS_HOST, KGS_DEVICE or KGS_HOST_ASYNC");
     DeviceGuard guard(h->device);
     if (!guard.ok) return cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     double* dst[4] = {P, Q, U, V};
+    const bool host = where != KGS_DEVICE;
     for (int f = 0; f < 4; ++f) {
-        double* d = (where == KGS_HOST) ? h->stage : dst[f];
+        double* d = host ? h->stage : dst[f];
         const void* src = (f < 2) ? h->pqb[h->cur] : h->uvb[h->cur];
         int n = (h->precision == 64)
                     ? launch_unpack<double>(h->M, d, (const double2*)src, f & 1, s, h->dim, h->N, f >= 2)
                     : launch_unpack<float>(h->M, d, (const float2*)src, f & 1, s, h->dim, h->N, f >= 2);
         if (n < 0) return cuda_fail(h, cudaGetLastError(), "unpack launch");
         h->launches += n;
-        if (where == KGS_HOST) {
+        if (host) {
             cudaError_t e = cudaMemcpyAsync(dst[f], h->stage, (size_t)h->M * sizeof(double),
                                             cudaMemcpyDeviceToHost, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "state download");

@@ -23,6 +23,7 @@ LIB_PATH = os.environ.get("KGS_LIBRARY") or os.path.join(HERE, "libkgs.so")
 KGS_OK = 0
 KGS_HOST = 0
 KGS_DEVICE = 1
+KGS_HOST_ASYNC = 2
 KGS_FP64 = 64
 KGS_FP32 = 32
 KGS_OPT_KERNEL = 1
@@ -42,6 +43,7 @@ KGS_OPT_WAVE_CHUNK = 14
 KGS_OPT_PDL = 15
 KGS_OPT_STREAM_CHUNK = 16
 KGS_OPT_STREAM_PREFETCH = 17
+KGS_ERR_ARG = -1
 KGS_ERR_TIMEOUT = -6
 
 # Every function the header declares, with its ctypes signature.
@@ -209,16 +211,26 @@ class Solver:
         self.close()
 
     # state ---------------------------------------------------------------
-    def set_state(self, P, Q, U, V, stream=None):
+    def set_state(self, P, Q, U, V, stream=None, asynchronous=False):
+        """Copy a state in.  asynchronous=True with host arrays queues the copy
+        on `stream` and returns at once (KGS_HOST_ASYNC): the arrays (pinned,
+        for the copy to overlap other work) must stay unchanged until the
+        stream has passed it."""
         where, ptrs, _keep = _as_buffers((P, Q, U, V), self.N, self.dim)
+        if asynchronous and where == KGS_HOST:
+            where = KGS_HOST_ASYNC
         _check(self._lib.kgs_set_state(self._h, *ptrs, where, _stream_ptr(stream)))
 
-    def get_state(self, out=None, stream=None):
+    def get_state(self, out=None, stream=None, asynchronous=False):
         """Return (P, Q, U, V).  With out=None, new numpy arrays; otherwise fills
-        the four given numpy arrays or CUDA tensors."""
+        the four given numpy arrays or CUDA tensors.  asynchronous=True with
+        host arrays queues the copy on `stream` (KGS_HOST_ASYNC): the arrays
+        hold the state once the stream has passed it."""
         if out is None:
             out = tuple(np.empty((self.N,) * self.dim) for _ in range(4))
         where, ptrs, _keep = _as_buffers(out, self.N, self.dim)
+        if asynchronous and where == KGS_HOST:
+            where = KGS_HOST_ASYNC
         _check(self._lib.kgs_get_state(self._h, *ptrs, where, _stream_ptr(stream)))
         return tuple(out)
 
