@@ -77,11 +77,13 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 # full grid (2D: a RED_FUSED pass of the 2048^2 grid; 3D: a launch of the
 # 512^3 grid, one-pass metrics), for the kernels as they are now, keyed by
 # (workload, precision, kernel: "pass" = one launch per colour pass, "stream"
-# = a step's two passes per launch); None where no capture exists.
+# = a step's two passes per launch, "stream2" = a step pair's four passes per
+# launch); None where no capture exists.
 NCU_TRAFFIC = {("2d", "fp64", "pass"): 117.52e6 + 25.74e6,
                ("3d", "fp64", "pass"): 3.7645e9 + 2.1086e9,
                ("3d", "fp32", "pass"): 1.8822e9 + 1.0321e9,
-               ("3d", "fp32", "stream"): 2.2622e9 + 2.1531e9}
+               ("3d", "fp32", "stream"): 2.2622e9 + 2.1531e9,
+               ("3d", "fp32", "stream2"): 2.5402e9 + 2.1779e9}
 
 
 # Issue-slot view of the float64 colour passes: the fraction of peak each
@@ -97,14 +99,14 @@ NCU_PIPES = {("2d", "fp64", "pass"): {"fp64": 0.874, "alu": 0.746, "fma": 0.129,
 def kernel_name(args, precision=None):
     """The dominant kernel of a solve: what KGS_OPT_KERNEL selects (0 = the
     library's automatic choice, which streams float32 3D grids whose N is a
-    multiple of 64, up to 1024, and makes one launch per pass otherwise;
-    "stream2": two steps per launch, KGS_OPT_KERNEL 8)."""
+    multiple of 64, up to 1024, two steps per launch ("stream2"), and makes
+    one launch per pass otherwise; "stream": one step per launch)."""
     precision = precision or args.precision
     n = args.grid_n or {"1d": 512, "2d": 2048, "3d": 512}.get(args.workload, 0)
     streams = args.workload == "3d" and precision == "fp32" and n % 64 == 0 and 64 <= n <= 1024
-    if args.kernel == 8:
+    if args.kernel == 8 or (args.kernel == 0 and streams):
         return "stream2" if streams else "pass"
-    if args.kernel == 7 or (args.kernel == 0 and streams):
+    if args.kernel == 7:
         return "stream" if streams else "pass"
     return "pass" if args.kernel in (0, 1) else None
 
@@ -119,6 +121,11 @@ def traffic_of(args, precision=None):
     if k is None:
         return None
     return NCU_TRAFFIC.get((args.workload, precision or args.precision, k))
+
+
+# Issue-active fraction of the two-step streamed kernel (smsp__issue_active,
+# ncu --set full of one 256^3 launch of the current kernel).
+NCU_ISSUE_STREAM2 = 0.622
 
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of
@@ -822,6 +829,18 @@ def main():
         got = final_state_dev(s32, prob)
         e2e32 = e2e_leg(s32, stream32, work, flush, world, args.steps, lambda: make_solver("fp32"))
         s32.close()
+        one_step = None
+        if kernel_name(args, "fp32") == "stream2":
+            # the one-step streamed kernel beside it: DRAM-bound where the
+            # two-step one is bound by instruction issue
+            args1 = argparse.Namespace(**vars(args))
+            args1.kernel = 7
+            leg1, s1, _ = solo_leg(args1, work, "fp32", init_dev, flush, local, dist, world,
+                                   min(args.steps, 3), 1)
+            s1.close()
+            one_step = {"value": leg1["value"], "unit": UNIT, "kernel": 7, "roofline": leg1["roofline"],
+                        "kernel_ms_per_launch": leg1["kernel_ms_per_launch"], "gpu_launches": leg1["gpu_launches"],
+                        "clocks": leg1["clocks"]}
         errs = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(got, ref)]
         del got, ref
         line["fp32"] = {
@@ -836,6 +855,13 @@ def main():
             "note": "error of the FP32-state run against the FP64 run from the same initial state, "
                     "per field max|x32 - x64| / max|x64| after the whole solve",
         }
+        if one_step is not None:
+            line["fp32"]["roofline"]["note"] = (
+                "two steps per launch (temporal depth 2): one read and one write of the state per two "
+                "steps, 16 B per point-update; bound by instruction issue, not DRAM (ncu 256^3: "
+                f"{NCU_ISSUE_STREAM2:.0%} issue-active); one_step: the DRAM-bound one-step kernel")
+            line["fp32"]["one_step"] = one_step
+            line["gpu_launches"] += one_step["gpu_launches"]
         line["gpu_launches"] += leg32["gpu_launches"]
     else:
         s.close()

@@ -63,6 +63,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "kgs_internal.h"
@@ -492,18 +493,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t off0 = (int64_t)(y + kG) * cols + zh + 2;
         const int64_t offr = pr2 >= 0 ? (int64_t)pr2 * cols + zh + 2 : -1;
         const int64_t offc = pc2 >= 0 ? (int64_t)(y + kG) * cols + pc2 : -1;
-        const int64_t offrc = (pr2 >= 0 && pc2 >= 0) ? (int64_t)pr2 * cols + pc2 : -1;
-        auto store = [&](int col, int x, float4 v) {
-            float4* pl = dst + ((int64_t)col * N + x) * plane_elems;
-            if (!kgs_in_bounds(x >= 0 && x < N && off0 < plane_elems && offr < plane_elems && offc < plane_elems &&
-                                   offrc < plane_elems,
-                               4u))
-                return;
-            pl[off0] = v;
-            if (offr >= 0) pl[offr] = v;
-            if (offc >= 0) pl[offc] = v;
-            if (offrc >= 0) pl[offrc] = v;
-        };
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (int j = 0; j < kSlots2 && j <= L + 7; ++j) issue(j);
@@ -513,7 +502,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 3; ++j) bad |= !wait(j);
         failed = __syncthreads_or(bad);
         float4 hA = make_float4(0.f, 0.f, 0.f, 0.f), hB = hA;  // this position's B2 values, one and two iterations back
-        for (int it = 0; it <= L + 5 && !failed; ++it) {
+        // output offsets of a tile point at B2's and R2's planes, advanced one
+        // plane per iteration (B2 on plane x0 - 5 + it, R2 on x0 - 6 + it), and
+        // its ghost copies' offsets relative to them
+        int64_t oB = ((int64_t)cB * N + x0 - 5) * plane_elems + off0;
+        int64_t oR = ((int64_t)cR * N + x0 - 6) * plane_elems + off0;
+        const int dgr = offr >= 0 ? (int)(offr - off0) : 0, dgc = offc >= 0 ? (int)(offc - off0) : 0;
+        const bool ghost = offr >= 0 || offc >= 0;
+        auto put = [&](int64_t o, float4 v) {
+            const int64_t end = 2 * (int64_t)N * plane_elems;
+            if (!kgs_in_bounds(o >= 0 && o < end && o + dgr >= 0 && o + dgr < end && o + dgc >= 0 &&
+                                   o + dgc < end && o + dgr + dgc >= 0 && o + dgr + dgc < end,
+                               4u))
+                return;
+            dst[o] = v;
+            if (ghost) {
+                if (dgr) dst[o + dgr] = v;
+                if (dgc) dst[o + dgc] = v;
+                if (dgr && dgc) dst[o + dgr + dgc] = v;
+            }
+        };
+        // one iteration; s0 = it % kSlots2 as a compile-time constant (the loop
+        // below is unrolled six times), so every slot address is fixed
+        auto body = [&](auto s0c, int it) {
+            constexpr int s0 = decltype(s0c)::value;
+            constexpr int jm2 = (s0 + 4) % kSlots2, jm1 = (s0 + 5) % kSlots2, jp1 = (s0 + 1) % kSlots2,
+                          jp2 = (s0 + 2) % kSlots2, jp3 = (s0 + 3) % kSlots2;
             // the slot of staged plane it - 3 is read no more: load plane it + 3 into it
             if (it >= 3 && threadIdx.x == 0) {
                 if (it + 3 <= L + 7) {
@@ -522,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (pf > 0 && it + 3 + pf <= L + 7) prefetch(it + 3 + pf);
             }
-            const int a = x0 - 3 + it;  // B1's plane (only its parity and, for stores, a - 2 and a - 3 matter)
+            const int a = x0 - 3 + it;  // B1's plane (only its parity matters here)
             const int ap = a & 1;
             int sr, sc, d;
             if (is_main) {
@@ -535,11 +549,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sc = (int)((e >> 5) & 63u);
                 d = (e & 0x8000u) ? (int)((e >> 11) & 3u) + 1 : 0;
             }
-            float4* Sm2 = slots + ((it + kSlots2 - 2) % kSlots2) * kSlotElems2;  // staged it - 2: R2's plane
-            float4* Sm1 = slots + ((it + kSlots2 - 1) % kSlots2) * kSlotElems2;  // staged it - 1: B2's
-            float4* Sz = slots + (it % kSlots2) * kSlotElems2;                   // staged it: R1's
-            float4* Sp1 = slots + ((it + 1) % kSlots2) * kSlotElems2;            // staged it + 1: B1's
-            const float4* Sp2 = slots + ((it + 2) % kSlots2) * kSlotElems2;
+            float4* Sm2 = slots + jm2 * kSlotElems2;       // staged it - 2: R2's plane
+            float4* Sm1 = slots + jm1 * kSlotElems2;       // staged it - 1: B2's
+            float4* Sz = slots + s0 * kSlotElems2;         // staged it: R1's
+            float4* Sp1 = slots + jp1 * kSlotElems2;       // staged it + 1: B1's
+            const float4* Sp2 = slots + jp2 * kSlotElems2;
             const int at = sr * kKK + sc;
             if (d >= 1)  // B1, plane a: red neighbours of the input state
                 Sp1[cB * kRR2 * kKK + at] =
@@ -551,20 +565,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (d >= 3 && it >= 4) {  // B2, plane a - 2: red of R1
                 cur = stream_point<BLACK_FUSED, kRR2>(Sm1, Sm2, Sz, cB, sr, sc, (cB ^ ap ^ yp ^ sr) & 1, c);
                 Sm1[cB * kRR2 * kKK + at] = cur;
-                if (d == 4 && a - 2 >= x0 && a - 2 < x0 + L) store(cB, a - 2, cur);
+                if (d == 4 && it >= 5 && it < L + 5) put(oB, cur);  // planes x0 .. x0 + L - 1
             }
             if (d == 4) {
                 if (it >= 6)  // R2, plane a - 3: black of B2 (below from two iterations back, above just made)
-                    store(cR, a - 3,
-                          stream_point_v<REDMODE, kRR2>(Sm2, hB, cur, cR, sr, sc, (cR ^ ap ^ 1 ^ yp ^ sr) & 1, c));
+                    put(oR, stream_point_v<REDMODE, kRR2>(Sm2, hB, cur, cR, sr, sc, (cR ^ ap ^ 1 ^ yp ^ sr) & 1, c));
                 hB = hA;
                 hA = cur;
             }
+            oB += plane_elems;
+            oR += plane_elems;
             // the next B1 needs staged plane it + 3 (its upper neighbours)
             bad = 0;
             if (stall && first && it == 1) bad = !mbar_wait_bounded(&bars[kSlots2], 0);  // never completes
-            if (!bad && it + 3 <= L + 7) bad = !wait(it + 3);
+            if (!bad && it + 3 <= L + 7) {
+                const bool ok = mbar_wait_bounded(&bars[jp3], (phase >> jp3) & 1u);
+                if (ok) {
+                    phase ^= 1u << jp3;
+                    if (threadIdx.x == 0) pending &= ~(1u << jp3);
+                }
+                bad = !ok;
+            }
             failed = __syncthreads_or(bad);
+        };
+        for (int it = 0;;) {
+            body(std::integral_constant<int, 0>{}, it);
+            if (++it > L + 5 || failed) break;
+            body(std::integral_constant<int, 1>{}, it);
+            if (++it > L + 5 || failed) break;
+            body(std::integral_constant<int, 2>{}, it);
+            if (++it > L + 5 || failed) break;
+            body(std::integral_constant<int, 3>{}, it);
+            if (++it > L + 5 || failed) break;
+            body(std::integral_constant<int, 4>{}, it);
+            if (++it > L + 5 || failed) break;
+            body(std::integral_constant<int, 5>{}, it);
+            if (++it > L + 5 || failed) break;
         }
         first = false;
     }

@@ -50,10 +50,14 @@ def test_traffic_only_for_the_captured_launches(bench):
     T = bench.NCU_TRAFFIC
     assert bench.traffic_of(_args()) == T[("2d", "fp64", "pass")]
     assert bench.traffic_of(_args(kernel=1, workload="3d", precision="fp32")) == T[("3d", "fp32", "pass")]
-    # auto on a float32 3D grid streams; so does kernel 7
-    assert bench.kernel_name(_args(workload="3d", precision="fp32")) == "stream"
-    assert bench.traffic_of(_args(workload="3d", precision="fp32")) == T[("3d", "fp32", "stream")]
+    # auto on a float32 3D grid streams two steps per launch (kernel 8); kernel 7 one
+    assert bench.kernel_name(_args(workload="3d", precision="fp32")) == "stream2"
+    assert bench.kernel_name(_args(kernel=8, workload="3d", precision="fp32")) == "stream2"
+    assert bench.traffic_of(_args(workload="3d", precision="fp32")) == T.get(("3d", "fp32", "stream2"))
     assert bench.traffic_of(_args(kernel=7, workload="3d", precision="fp32")) == T[("3d", "fp32", "stream")]
+    assert bench.temporal_depth(_args(workload="3d", precision="fp32")) == 2
+    assert bench.temporal_depth(_args(kernel=7, workload="3d", precision="fp32")) == 1
+    assert bench.bytes_per_point_update(4, 2) == 16
     assert bench.kernel_name(_args(kernel=7, workload="3d", precision="fp64")) == "pass"
     assert bench.traffic_of(_args(workload="3d")) == T[("3d", "fp64", "pass")]
     assert bench.traffic_of(_args(kernel=6)) is None          # another kernel

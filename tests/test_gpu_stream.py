@@ -60,24 +60,6 @@ def test_streamed_planes_one_row_last_tile():
     assert inv_got == inv_want
 
 
-def test_streamed_planes_are_the_default_for_fp32_3d():
-    """KGS_OPT_KERNEL 0 (auto) takes the streamed planes for a float32 3D grid
-    it fits: bitwise kernel 7's state and launch count."""
-    prob = Problem(3, 64, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
-    st = random_state(prob, 2502_09537 + 311, 0.5)
-    counts = []
-    for kernel in (0, STREAM):
-        with Solver.from_problem(prob, KGS_FP32) as s:
-            s.set_option(KGS_OPT_KERNEL, kernel)
-            s.set_state(*[np.array(a, copy=True) for a in st])
-            l0 = s.launch_count
-            s.step(6)
-            counts.append((s.launch_count - l0, s.get_state()))
-    assert counts[0][0] == counts[1][0] == 6 + 3
-    for x, y in zip(counts[0][1], counts[1][1]):
-        assert np.array_equal(x, y)
-
-
 def test_streamed_planes_negative_kappa1_and_bumps():
     """The Sec. 5.2 parameters (kappa1 < 0) on its ellipsoid data."""
     w = inputs.paper_exp3_ellipsoids_3d(64, 0.01, 9)

@@ -72,6 +72,20 @@ def test_launch_counts():
         assert launches == want, (n, launches)
 
 
+def test_two_step_launches_are_the_default_for_fp32_3d():
+    """KGS_OPT_KERNEL 0 (auto) takes two steps per launch for a float32 3D
+    grid it fits: kernel 8's launch count, and bitwise the state of kernels 8
+    and 7."""
+    prob = Problem(3, 64, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
+    st = random_state(prob, 2502_09537 + 311, 0.5)
+    runs = [run(prob, st, [6], k) for k in (0, STREAM2, 7)]
+    assert runs[0][2] == runs[1][2] == 6 / 2 + 3
+    assert runs[2][2] == 6 + 3
+    for r in runs[1:]:
+        for x, y in zip(runs[0][0], r[0]):
+            assert np.array_equal(x, y)
+
+
 def test_two_step_launches_negative_kappa1_and_bumps():
     """The Sec. 5.2 parameters (kappa1 < 0) on its ellipsoid data."""
     w = inputs.paper_exp3_ellipsoids_3d(64, 0.01, 9)
