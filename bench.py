@@ -82,7 +82,7 @@ def algorithmic_flops_per_point_update(dim: int) -> float:
 NCU_TRAFFIC = {("2d", "fp64", "pass"): 117.52e6 + 25.74e6,
                ("3d", "fp64", "pass"): 3.7645e9 + 2.1086e9,
                ("3d", "fp32", "pass"): 1.8822e9 + 1.0321e9,
-               ("3d", "fp32", "stream"): 2.2622e9 + 2.1531e9,
+               ("3d", "fp32", "stream"): 2.4073e9 + 2.1756e9,
                ("3d", "fp32", "stream2"): 2.5402e9 + 2.1779e9}
 
 

@@ -270,18 +270,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t off0 = (int64_t)(y + kG) * cols + zh + 2;
         const int64_t offr = pr2 >= 0 ? (int64_t)pr2 * cols + zh + 2 : -1;
         const int64_t offc = pc2 >= 0 ? (int64_t)(y + kG) * cols + pc2 : -1;
-        const int64_t offrc = (pr2 >= 0 && pc2 >= 0) ? (int64_t)pr2 * cols + pc2 : -1;
-        auto store = [&](int col, int x, float4 v) {
-            float4* pl = dst + ((int64_t)col * N + x) * plane_elems;
-            if (!kgs_in_bounds(x >= 0 && x < N && off0 < plane_elems && offr < plane_elems && offc < plane_elems &&
-                                   offrc < plane_elems,
-                               4u))
-                return;
-            pl[off0] = v;
-            if (offr >= 0) pl[offr] = v;
-            if (offc >= 0) pl[offc] = v;
-            if (offrc >= 0) pl[offrc] = v;
-        };
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (int j = 0; j < kSlots - 1 && j <= L + 3; ++j) issue(j);
@@ -291,25 +279,51 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 3; ++j) bad |= !wait(j);
         failed = __syncthreads_or(bad);
         const int r = 2 + t, k = 2 + lane;
-        for (int it = 0; it <= L + 1 && !failed; ++it) {
+        // output offsets of this thread's point at the red pass's plane (x0 - 2 +
+        // it), advanced one plane per iteration, and its ghost copies' offsets
+        // relative to them
+        int64_t oR_out = ((int64_t)cR * N + x0 - 2) * plane_elems + off0;
+        int64_t oB_out = ((int64_t)cB * N + x0 - 2) * plane_elems + off0;
+        const int dgr = offr >= 0 ? (int)(offr - off0) : 0, dgc = offc >= 0 ? (int)(offc - off0) : 0;
+        const bool ghost = offr >= 0 || offc >= 0;
+        auto put = [&](int64_t o, float4 v) {
+            const int64_t end = 2 * (int64_t)N * plane_elems;
+            if (!kgs_in_bounds(o >= 0 && o < end && o + dgr >= 0 && o + dgr < end && o + dgc >= 0 &&
+                                   o + dgc < end && o + dgr + dgc >= 0 && o + dgr + dgc < end,
+                               4u))
+                return;
+            dst[o] = v;
+            if (ghost) {
+                if (dgr) dst[o + dgr] = v;
+                if (dgc) dst[o + dgc] = v;
+                if (dgr && dgc) dst[o + dgr + dgc] = v;
+            }
+        };
+        // one iteration; s0 = it % kSlots as a compile-time constant (the loop
+        // below is unrolled six times), so every slot address is fixed
+        auto body = [&](auto s0c, int it) {
+            constexpr int s0 = decltype(s0c)::value;
+            constexpr int jm1 = (s0 + kSlots - 1) % kSlots, jp1 = (s0 + 1) % kSlots, jp2 = (s0 + 2) % kSlots,
+                          jp3 = (s0 + 3) % kSlots;
             const int cb = x0 - 1 + it;  // black plane; red plane cb - 1
             // black pass on plane cb (staged j = it + 1), red neighbours in j = it, it + 2:
             // this thread's interior point (r, k)
-            const float4* sb = slots + ((it + 1) % kSlots) * kSlotElems;
-            const float4* sbd = slots + (it % kSlots) * kSlotElems;
-            const float4* sbu = slots + ((it + 2) % kSlots) * kSlotElems;
+            const float4* sb = slots + jp1 * kSlotElems;
+            const float4* sbd = slots + s0 * kSlotElems;
+            const float4* sbu = slots + jp2 * kSlotElems;
             float4* wb = const_cast<float4*>(sb) + cB * kRR * kKK;
             if (t < ty) wb[r * kKK + k] = stream_point<BLACK_FUSED>(sb, sbd, sbu, cB, r, k, (cB ^ cb ^ yp ^ r) & 1, c);
             // red pass on plane cb - 1 (staged j = it), black neighbours in j = it - 1, it + 1:
             // its point (r, k) needs black (cb) only at (r, k), just written by this thread
             if (it >= 2 && t < ty) {
                 const int x = cb - 1;
-                const float4* sr = slots + (it % kSlots) * kSlotElems;
-                const float4* srd = slots + ((it + kSlots - 1) % kSlots) * kSlotElems;
-                const float4 a = stream_point<REDMODE>(sr, srd, sb, cR, r, k, (cR ^ x ^ yp ^ r) & 1, c);
-                store(cR, x, a);
-                store(cB, x, sr[cB * kRR * kKK + r * kKK + k]);
+                const float4* sr = slots + s0 * kSlotElems;
+                const float4* srd = slots + jm1 * kSlotElems;
+                put(oR_out, stream_point<REDMODE>(sr, srd, sb, cR, r, k, (cR ^ x ^ yp ^ r) & 1, c));
+                put(oB_out, sr[cB * kRR * kKK + r * kKK + k]);
             }
+            oR_out += plane_elems;
+            oB_out += plane_elems;
             // the ring of black points of plane cb that the red pass of plane cb
             // reads (next iteration): rows 1 and ty + 2, and per row the one
             // column beyond the tile on the side its red points' last-axis
@@ -328,7 +342,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the next black pass needs staged plane it + 3 (its upper neighbours)
             bad = 0;
             if (stall && first && it == 1) bad = !mbar_wait_bounded(&bars[kSlots], 0);  // never completes
-            if (!bad && it + 3 <= L + 3) bad = !wait(it + 3);
+            if (!bad && it + 3 <= L + 3) {
+                const bool ok = mbar_wait_bounded(&bars[jp3], (phase >> jp3) & 1u);
+                if (ok) {
+                    phase ^= 1u << jp3;
+                    if (threadIdx.x == 0) pending &= ~(1u << jp3);
+                }
+                bad = !ok;
+            }
             failed = __syncthreads_or(bad);
             // staged plane it - 1 is no longer read: load plane it - 1 + kSlots into its
             // slot, and prefetch the plane pf beyond it into L2
@@ -339,6 +360,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (pf > 0 && it + kSlots - 1 + pf <= L + 3) prefetch(it + kSlots - 1 + pf);
             }
+        };
+        for (int it = 0; it <= L + 1 && !failed;) {
+            body(std::integral_constant<int, 0>{}, it);
+            if (++it > L + 1 || failed) break;
+            body(std::integral_constant<int, 1>{}, it);
+            if (++it > L + 1 || failed) break;
+            body(std::integral_constant<int, 2>{}, it);
+            if (++it > L + 1 || failed) break;
+            body(std::integral_constant<int, 3>{}, it);
+            if (++it > L + 1 || failed) break;
+            body(std::integral_constant<int, 4>{}, it);
+            if (++it > L + 1 || failed) break;
+            body(std::integral_constant<int, 5>{}, it);
+            ++it;
         }
         first = false;
     }
