@@ -83,7 +83,7 @@ NCU_TRAFFIC = {("2d", "fp64", "pass"): 117.52e6 + 25.74e6,
                ("3d", "fp64", "pass"): 3.7645e9 + 2.1086e9,
                ("3d", "fp32", "pass"): 1.8822e9 + 1.0321e9,
                ("3d", "fp32", "stream"): 2.4073e9 + 2.1756e9,
-               ("3d", "fp32", "stream2"): 2.5402e9 + 2.1779e9}
+               ("3d", "fp32", "stream2"): 2.5981e9 + 2.1786e9}
 
 
 # Issue-slot view of the float64 colour passes: the fraction of peak each
@@ -125,7 +125,7 @@ def traffic_of(args, precision=None):
 
 # Issue-active fraction of the two-step streamed kernel (smsp__issue_active,
 # ncu --set full of one 256^3 launch of the current kernel).
-NCU_ISSUE_STREAM2 = 0.622
+NCU_ISSUE_STREAM2 = 0.656
 
 
 # FP64 pipe of the B300: 2 FMA per cycle per SM (ncu: peak_sustained of

@@ -85,6 +85,7 @@ constexpr int kWarps = 32;               // warp t < kTy: tile row t; warps kTy 
 constexpr int kThreads = 32 * kWarps;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr size_t kSmemBytes = (size_t)kSlots * kSlotElems * sizeof(float4) + (kSlots + 1) * sizeof(uint64_t);
+static_assert(kSlotElems * sizeof(float4) % 128 == 0, "one-step kernel: TMA slots 128-byte aligned");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -154,17 +155,17 @@ __device__ __forceinline__ void tma_prefetch_plane(const CUtensorMap* map, int c
 // colour at the same staged position in the planes below and above); zp = the
 // point's last-axis parity, which places its two last-axis neighbours at
 // columns k-1+zp, k+zp.
-template <int MODE, int RR>
+template <int MODE, int RR, int KK = kKK>
 __device__ __forceinline__ float4 stream_point_v(const float4* s, float4 ndn, float4 nup, int own_c, int r, int k,
                                                  int zp, const Coef<float>& c)
 {
-    const int oth = (own_c ^ 1) * RR * kKK;
-    const int at = r * kKK + k;
-    if (!kgs_in_bounds(r >= 1 && r + 1 < RR && k - 1 + zp >= 0 && k + zp < kKK && zp >= 0 && zp <= 1 &&
+    const int oth = (own_c ^ 1) * RR * KK;
+    const int at = r * KK + k;
+    if (!kgs_in_bounds(r >= 1 && r + 1 < RR && k - 1 + zp >= 0 && k + zp < KK && zp >= 0 && zp <= 1 &&
                            own_c >= 0 && own_c <= 1,
                        2u))
         return make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 n[6] = {ndn, nup, s[oth + at - kKK], s[oth + at + kKK], s[oth + at - 1 + zp], s[oth + at + zp]};
+    const float4 n[6] = {ndn, nup, s[oth + at - KK], s[oth + at + KK], s[oth + at - 1 + zp], s[oth + at + zp]};
     float p[6], q[6], w[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
@@ -172,22 +173,22 @@ __device__ __forceinline__ float4 stream_point_v(const float4* s, float4 ndn, fl
         q[m] = n[m].y;
         w[m] = n[m].z;
     }
-    float4 a = s[own_c * RR * kKK + at];
+    float4 a = s[own_c * RR * KK + at];
     update_point<float, 3, MODE>(c, nsum_scaled(p, c.beta), nsum_scaled(q, c.beta), nsum_scaled(w, c.Bp), a.x, a.y,
                                  a.z, a.w);
     return a;
 }
 
 // The same with the axis-0 neighbours read from the slots dn / up.
-template <int MODE, int RR = kRR>
+template <int MODE, int RR = kRR, int KK = kKK>
 __device__ __forceinline__ float4 stream_point(const float4* s, const float4* dn, const float4* up, int own_c, int r,
                                                int k, int zp, const Coef<float>& c)
 {
-    const int oth = (own_c ^ 1) * RR * kKK;
-    const int at = r * kKK + k;
-    if (!kgs_in_bounds(r >= 0 && r < RR && k >= 0 && k < kKK && own_c >= 0 && own_c <= 1, 2u))
+    const int oth = (own_c ^ 1) * RR * KK;
+    const int at = r * KK + k;
+    if (!kgs_in_bounds(r >= 0 && r < RR && k >= 0 && k < KK && own_c >= 0 && own_c <= 1, 2u))
         return make_float4(0.f, 0.f, 0.f, 0.f);
-    return stream_point_v<MODE, RR>(s, dn[oth + at], up[oth + at], own_c, r, k, zp, c);
+    return stream_point_v<MODE, RR, KK>(s, dn[oth + at], up[oth + at], own_c, r, k, zp, c);
 }
 
 template <int REDMODE>
@@ -425,11 +426,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 // they are made: black at B2, red at R2.
 constexpr int kTy2 = 23;                             // tile rows
 constexpr int kRR2 = kTy2 + 8;                       // staged rows
-constexpr int kSlotElems2 = 2 * kRR2 * kKK;          // float4 per staged plane
+constexpr int kKK2 = kKK + 1;                        // staged row pitch, 37 float4: see stream_make_map
+constexpr int kSlotElems2 = 2 * kRR2 * kKK2;         // float4 per staged plane
+constexpr int kSlotStride2 = (kSlotElems2 + 7) / 8 * 8;  // slots 128-byte aligned (a TMA destination must be)
 constexpr int kSlots2 = 6;
 constexpr int kMainWarps2 = kTy2 + 6;                // warp w: tile row w - 3
 constexpr int kSide2 = 32 * (kWarps - kMainWarps2);  // threads for the points beyond the tile's columns
-constexpr size_t kSmemBytes2 = (size_t)kSlots2 * kSlotElems2 * sizeof(float4) + (kSlots2 + 1) * sizeof(uint64_t);
+constexpr size_t kSmemBytes2 = (size_t)kSlots2 * kSlotStride2 * sizeof(float4) + (kSlots2 + 1) * sizeof(uint64_t);
+static_assert(kSlotStride2 * sizeof(float4) % 128 == 0, "two-step kernel: TMA slots 128-byte aligned");
 static_assert(kSmemBytes2 <= 232448, "two-step kernel: shared memory");
 static_assert(kRR2 <= 32, "two-step kernel: staged rows are five bits in the side list");
 
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4* slots = reinterpret_cast<float4*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kSlots2 * kSlotElems2 * sizeof(float4));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kSlots2 * kSlotStride2 * sizeof(float4));
     constexpr int cR = 0, cB = 1;  // 3D: red = even 0-based coordinate sum
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const bool is_main = w < kMainWarps2;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         auto issue = [&](int j) {
             const int s = j % kSlots2;
             mbar_expect_tx(&bars[s], (unsigned)(kSlotElems2 * sizeof(float4)));
-            tma_load_plane(slots + s * kSlotElems2, &src, &bars[s], 4 * zh0, y0 - 4 + kG, coords(j));
+            tma_load_plane(slots + s * kSlotStride2, &src, &bars[s], 4 * zh0, y0 - 4 + kG, coords(j));
             pending |= 1u << s;
         };
         auto prefetch = [&](int j) { tma_prefetch_plane(&src, 4 * zh0, y0 - 4 + kG, coords(j)); };
@@ -584,27 +588,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sc = (int)((e >> 5) & 63u);
                 d = (e & 0x8000u) ? (int)((e >> 11) & 3u) + 1 : 0;
             }
-            float4* Sm2 = slots + jm2 * kSlotElems2;       // staged it - 2: R2's plane
-            float4* Sm1 = slots + jm1 * kSlotElems2;       // staged it - 1: B2's
-            float4* Sz = slots + s0 * kSlotElems2;         // staged it: R1's
-            float4* Sp1 = slots + jp1 * kSlotElems2;       // staged it + 1: B1's
-            const float4* Sp2 = slots + jp2 * kSlotElems2;
-            const int at = sr * kKK + sc;
+            float4* Sm2 = slots + jm2 * kSlotStride2;       // staged it - 2: R2's plane
+            float4* Sm1 = slots + jm1 * kSlotStride2;       // staged it - 1: B2's
+            float4* Sz = slots + s0 * kSlotStride2;         // staged it: R1's
+            float4* Sp1 = slots + jp1 * kSlotStride2;       // staged it + 1: B1's
+            const float4* Sp2 = slots + jp2 * kSlotStride2;
+            const int at = sr * kKK2 + sc;
             if (d >= 1)  // B1, plane a: red neighbours of the input state
-                Sp1[cB * kRR2 * kKK + at] =
-                    stream_point<BLACK_FUSED, kRR2>(Sp1, Sz, Sp2, cB, sr, sc, (cB ^ ap ^ yp ^ sr) & 1, c);
+                Sp1[cB * kRR2 * kKK2 + at] =
+                    stream_point<BLACK_FUSED, kRR2, kKK2>(Sp1, Sz, Sp2, cB, sr, sc, (cB ^ ap ^ yp ^ sr) & 1, c);
             if (d >= 2 && it >= 2)  // R1, plane a - 1: black of B1
-                Sz[cR * kRR2 * kKK + at] =
-                    stream_point<RED_FUSED, kRR2>(Sz, Sm1, Sp1, cR, sr, sc, (cR ^ ap ^ 1 ^ yp ^ sr) & 1, c);
+                Sz[cR * kRR2 * kKK2 + at] =
+                    stream_point<RED_FUSED, kRR2, kKK2>(Sz, Sm1, Sp1, cR, sr, sc, (cR ^ ap ^ 1 ^ yp ^ sr) & 1, c);
             float4 cur = hA;
             if (d >= 3 && it >= 4) {  // B2, plane a - 2: red of R1
-                cur = stream_point<BLACK_FUSED, kRR2>(Sm1, Sm2, Sz, cB, sr, sc, (cB ^ ap ^ yp ^ sr) & 1, c);
-                Sm1[cB * kRR2 * kKK + at] = cur;
+                cur = stream_point<BLACK_FUSED, kRR2, kKK2>(Sm1, Sm2, Sz, cB, sr, sc, (cB ^ ap ^ yp ^ sr) & 1, c);
+                Sm1[cB * kRR2 * kKK2 + at] = cur;
                 if (d == 4 && it >= 5 && it < L + 5) put(oB, cur);  // planes x0 .. x0 + L - 1
             }
             if (d == 4) {
                 if (it >= 6)  // R2, plane a - 3: black of B2 (below from two iterations back, above just made)
-                    put(oR, stream_point_v<REDMODE, kRR2>(Sm2, hB, cur, cR, sr, sc, (cR ^ ap ^ 1 ^ yp ^ sr) & 1, c));
+                    put(oR, stream_point_v<REDMODE, kRR2, kKK2>(Sm2, hB, cur, cR, sr, sc, (cR ^ ap ^ 1 ^ yp ^ sr) & 1, c));
                 hB = hA;
                 hA = cur;
             }
@@ -877,7 +881,16 @@ int stream_make_map(void* buf, int64_t N, int steps, void* map_out)
     const cuuint64_t dims[4] = {(cuuint64_t)(4 * (hN + 4)), rows, (cuuint64_t)N, 2};
     const cuuint64_t row = (cuuint64_t)(hN + 4) * sizeof(float4);
     const cuuint64_t strides[3] = {row, row * rows, row * rows * (cuuint64_t)N};
-    const cuuint32_t box[4] = {4 * kKK, (cuuint32_t)(steps == 2 ? kRR2 : kRR), 1, 2};
+    // the two-step kernel's box is one float4 wider than the 36 columns it
+    // reads, so that its staged rows are 37 float4 apart in shared memory:
+    // 16-byte accesses fall into 8 groups of four banks by (pitch x row +
+    // column) mod 8, and a pitch of 36 put the points beyond a tile's columns
+    // (a few columns on many rows) into two of the eight groups (modelled:
+    // 84 wavefronts per warp and pass over them, 36 with a pitch of 37); in
+    // the grid's last tile column the extra float4 lies beyond the row and
+    // is zero-filled
+    const cuuint32_t box[4] = {(cuuint32_t)(steps == 2 ? 4 * kKK2 : 4 * kKK), (cuuint32_t)(steps == 2 ? kRR2 : kRR),
+                               1, 2};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     // a staged row is 4 kKK floats = 576 bytes = 9 x 64: L2 promotion to 64-byte
     // lines fetches exactly the row (256-byte promotion read 768 bytes per row,
