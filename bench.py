@@ -856,10 +856,15 @@ def main():
                     "per field max|x32 - x64| / max|x64| after the whole solve",
         }
         if one_step is not None:
-            line["fp32"]["roofline"]["note"] = (
+            roof = line["fp32"]["roofline"]
+            roof["note"] = (
                 "two steps per launch (temporal depth 2): one read and one write of the state per two "
-                "steps, 16 B per point-update; bound by instruction issue, not DRAM (ncu 256^3: "
-                f"{NCU_ISSUE_STREAM2:.0%} issue-active); one_step: the DRAM-bound one-step kernel")
+                "steps, 16 B per point-update; bound by shared-memory latency and instruction issue, "
+                f"not DRAM (ncu 256^3: {NCU_ISSUE_STREAM2:.0%} issue-active); one_step: the DRAM-bound "
+                "one-step kernel; equivalent_*: the bandwidth a one-step kernel (32 B per point-update) "
+                "would need for this kernel's rate")
+            roof["equivalent_one_step_gbs"] = roof["achieved"] * 2
+            roof["equivalent_one_step_frac"] = roof["frac"] * 2
             line["fp32"]["one_step"] = one_step
             line["gpu_launches"] += one_step["gpu_launches"]
         line["gpu_launches"] += leg32["gpu_launches"]
