@@ -739,7 +739,8 @@ def main():
     ap.add_argument("--kernel", type=int, default=0,
                     help="KGS_OPT_KERNEL: 0 auto, 1 pass, 2 shared memory, 3 tile, 4 persistent, "
                          "5 slab-pipelined passes, 6 wave (a step's two passes in one launch), "
-                         "7 streamed planes (3D FP32: a step's two passes per axis-0 plane, TMA-staged)")
+                         "7 streamed planes (3D FP32: a step's two passes per axis-0 plane, TMA-staged), "
+                         "8 streamed planes, two steps per launch (the 3D FP32 default)")
     ap.add_argument("--slab-planes", type=int, default=0, help="KGS_OPT_SLAB_PLANES (slab and wave kernels)")
     ap.add_argument("--stream-chunk", type=int, default=0, help="KGS_OPT_STREAM_CHUNK (streamed-plane kernel)")
     ap.add_argument("--stream-prefetch", type=int, default=-1,

@@ -99,7 +99,7 @@ struct kgs_solver {
     // for grids lex_sweep_applies takes, the strip sweep's progress counters
     int olex = 0;
     unsigned* lsync = nullptr;
-    // streamed-plane kernel (KGS_OPT_KERNEL 7): two packed copies of the state
+    // streamed-plane kernels (KGS_OPT_KERNEL 7, 8): two packed copies of the state
     // and their TMA tensor maps (CUtensorMap storage)
     void* sbuf[2] = {nullptr, nullptr};
     alignas(64) unsigned char smap[2][128] = {};
