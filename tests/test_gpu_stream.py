@@ -74,10 +74,12 @@ def test_streamed_planes_negative_kappa1_and_bumps():
     (Problem(3, 64, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4), KGS_FP64),   # float64 state
     (Problem(2, 128, 40.0, 1.0, 1.0, 1.0, 1.0, 5e-4), KGS_FP32),  # 2D
 ])
-def test_grids_it_does_not_take_run_the_passes(prob, precision):
+@pytest.mark.parametrize("kernel", [STREAM, STREAM + 1])
+def test_grids_it_does_not_take_run_the_passes(prob, precision, kernel):
+    """Kernels 7 and 8 (one and two steps per launch) on grids neither takes."""
     st = random_state(prob, 77, 0.5)
     want, _ = run(prob, st, [5], 1, precision)
-    got, _ = run(prob, st, [5], STREAM, precision)
+    got, _ = run(prob, st, [5], kernel, precision)
     for x, y in zip(got, want):
         assert np.array_equal(x, y)
 
