@@ -865,16 +865,17 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 
 int stream_make_map(void* buf, int64_t N, int steps, void* map_out)
 {
-    static EncodeTiled encode = nullptr;
-    if (!encode) {
+    // looked up once, thread-safely (a function-local static's initialisation)
+    static const EncodeTiled encode = []() -> EncodeTiled {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !fn)
-            return -1;
-        encode = reinterpret_cast<EncodeTiled>(fn);
-    }
+            return nullptr;
+        return reinterpret_cast<EncodeTiled>(fn);
+    }();
+    if (!encode) return -1;
     const int64_t hN = N / 2;
     // dims, innermost first: the floats of a padded row, rows, planes, colours
     const cuuint64_t rows = (cuuint64_t)(N + 2 * kG);
@@ -904,14 +905,11 @@ int stream_make_map(void* buf, int64_t N, int steps, void* map_out)
 int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, int red_mode, int* err, int stall,
                   int chunk, int prefetch, cudaStream_t s)
 {
-    static bool attr_set[2] = {false, false};
+    // the shared-memory allowance is a per-device function attribute: set it on
+    // every launch (a host call of microseconds, next to a launch of a millisecond)
     auto kern = red_mode == RED_ADJ ? stream_kernel<RED_ADJ> : stream_kernel<RED_FUSED>;
-    const int which = red_mode == RED_ADJ ? 1 : 0;
-    if (!attr_set[which]) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
-            return -1;
-        attr_set[which] = true;
-    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+        return -1;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -928,14 +926,11 @@ int launch_stream(const void* map, void* dst, int64_t N, const Coef<float>& c, i
 int launch_stream2(const void* map, const void* side, void* dst, int64_t N, const Coef<float>& c, int red_mode,
                    int* err, int stall, int chunk, int prefetch, cudaStream_t s)
 {
-    static bool attr_set[2] = {false, false};
+    // the shared-memory allowance is a per-device function attribute: set it on
+    // every launch (a host call of microseconds, next to a launch of a millisecond)
     auto kern = red_mode == RED_ADJ ? stream2_kernel<RED_ADJ> : stream2_kernel<RED_FUSED>;
-    const int which = red_mode == RED_ADJ ? 1 : 0;
-    if (!attr_set[which]) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes2) != cudaSuccess)
-            return -1;
-        attr_set[which] = true;
-    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes2) != cudaSuccess)
+        return -1;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
