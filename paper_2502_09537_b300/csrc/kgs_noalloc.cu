@@ -148,16 +148,14 @@ __global__ void __launch_bounds__(kThreads) noalloc_finalize_kernel(const double
 void* current_context()
 {
     using CtxGetCurrent = CUresult (*)(CUcontext*);
-    static CtxGetCurrent fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
+    static const CtxGetCurrent fn = []() -> CtxGetCurrent {  // looked up once, thread-safely
         void* f = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<CtxGetCurrent>(f);
-        looked = true;
-    }
+            return reinterpret_cast<CtxGetCurrent>(f);
+        return nullptr;
+    }();
     CUcontext ctx = nullptr;
     if (!fn || fn(&ctx) != CUDA_SUCCESS) return nullptr;
     return ctx;
