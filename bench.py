@@ -695,7 +695,8 @@ def e2e_leg(s, stream, work, flush, world, steps, make_solver):
             read[i] = torch.cuda.Event()
             read[i].record(down)
         down.synchronize()
-    e2e_s = time.perf_counter() - t0
+    from paper_2502_09537_b300.dist import max_over_ranks
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")  # the slowest rank's time
     other.close()
     del host_in, host_out
     return {"value": world * prob.points * work.nsteps * n / e2e_s, "unit": UNIT,
