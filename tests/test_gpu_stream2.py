@@ -146,3 +146,37 @@ def test_two_step_wait_timeout_is_reported_and_the_context_survives():
     got, _, _ = run(prob, st, [4], STREAM2)
     for x, y in zip(got, want):
         assert np.array_equal(x, y)
+
+
+def test_largest_grid_both_streamed_kernels_are_the_pass_kernel():
+    """N = 1024, the largest grid the streamed kernels take (4.3e9 float4 of
+    packed state, tensor-map strides of 8.7 GB per colour): two and three
+    steps (one two-step launch; two and one), compared on the device with the
+    pass kernel's state bit for bit.  Inputs are drawn on the device; one
+    handle exists at a time (about 61 GB each with the packed copies)."""
+    N = 1024
+    prob = Problem(3, N, 20.0, 1.1, 0.9, 1.2, 0.8, 5e-4 * (512 / N) ** 2)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2502_09537 + N)
+    init = [0.5 * (torch.rand((N,) * 3, dtype=torch.float64, device="cuda", generator=g) - 0.5)
+            for _ in range(4)]
+
+    def final(kernel, nsteps):
+        out = [torch.empty_like(a) for a in init]
+        with Solver.from_problem(prob, KGS_FP32) as s:
+            s.set_option(KGS_OPT_KERNEL, kernel)
+            s.set_state(*init)
+            s.step(nsteps)
+            s.get_state(out)
+            torch.cuda.synchronize()
+        return out
+
+    for nsteps in (2, 3):
+        want = final(1, nsteps)
+        for kernel in (STREAM2, 7):
+            got = final(kernel, nsteps)
+            for x, y in zip(got, want):
+                assert torch.equal(x, y), (kernel, nsteps)
+            del got
+        del want
+        torch.cuda.empty_cache()
