@@ -99,12 +99,12 @@ NCU_PIPES = {("2d", "fp64", "pass"): {"fp64": 0.874, "alu": 0.746, "fma": 0.129,
 def kernel_name(args, precision=None):
     """The dominant kernel of a solve: what KGS_OPT_KERNEL selects (0 = the
     library's automatic choice, which streams float32 3D grids whose N is a
-    multiple of 64, up to 1024, two steps per launch ("stream2"), and makes
-    one launch per pass otherwise; "stream": one step per launch)."""
+    multiple of 64 from 128 to 1024, two steps per launch ("stream2"), and
+    makes one launch per pass otherwise; "stream": one step per launch)."""
     precision = precision or args.precision
     n = args.grid_n or {"1d": 512, "2d": 2048, "3d": 512}.get(args.workload, 0)
     streams = args.workload == "3d" and precision == "fp32" and n % 64 == 0 and 64 <= n <= 1024
-    if args.kernel == 8 or (args.kernel == 0 and streams):
+    if args.kernel == 8 or (args.kernel == 0 and streams and n >= 128):
         return "stream2" if streams else "pass"
     if args.kernel == 7:
         return "stream" if streams else "pass"

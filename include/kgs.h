@@ -92,8 +92,8 @@ extern "C" {
                                four-row halo (temporal depth 2: one read and one write of the
                                state per two steps; an odd step count ends with one launch of
                                7; same grids and buffers as 7).  Auto picks 2 for grids that fit
-                               one CTA's shared memory, 8 where it applies, 1 otherwise.  All
-                               give bitwise the same state. */
+                               one CTA's shared memory, 8 where it applies and N >= 128, 1
+                               otherwise.  All give bitwise the same state. */
 #define KGS_OPT_GRAPH    2  /* 0 off, 1 replay colour passes from a CUDA graph (default 1) */
 #define KGS_OPT_THREADS  3  /* CTA size of the colour-pass kernels: 128, 256 (default), 512 */
 #define KGS_OPT_PPT      4  /* points of one colour per thread in those kernels: 1 only (2 was

@@ -231,11 +231,11 @@ int kernel_choice(const kgs_solver* h)
     const int64_t cap = smem_resident_max_points(h->precision == 64 ? 8 : 4);
     if (h->opt_kernel >= K_PASS && h->opt_kernel <= K_STREAM2) return h->opt_kernel;
     if (h->M <= cap) return K_SMEM;
-    // Float32 3D grids the streamed-plane kernels take: two steps per launch
-    // (measured at 512^3: 1.39e11 point-updates/s, against 1.27e11 for a
-    // step's two passes per launch, 0.73 of HBM, and 1.085e11 for two pass
-    // launches per step).
-    if (stream_applies(h->dim, h->N, h->precision)) return K_STREAM2;
+    // Float32 3D grids the streamed-plane kernels take, from N = 128: two steps
+    // per launch (measured, point-updates/s against one launch per pass: 512^3
+    // 1.46e11 / 1.09e11, 256^3 1.22e11 / 1.01e11, 128^3 6.6e10 / 5.2e10; at
+    // 64^3 the grid's 3 tiles leave most SMs idle: 9.4e9 / 2.3e10).
+    if (stream_applies(h->dim, h->N, h->precision) && h->N >= 128) return K_STREAM2;
     // Otherwise, measured on B300 (3D 512^3 / 2D 2048^2): one launch per pass
     // beats the temporally blocked tiles in both precisions (FP32: 8.6e10 vs
     // 6.2e10 / 9.8e10 vs 3.4e10 point-updates/s; FP64: 1.0e10 vs 6.1e9), so

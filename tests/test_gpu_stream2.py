@@ -74,9 +74,9 @@ def test_launch_counts():
 
 def test_two_step_launches_are_the_default_for_fp32_3d():
     """KGS_OPT_KERNEL 0 (auto) takes two steps per launch for a float32 3D
-    grid it fits: kernel 8's launch count, and bitwise the state of kernels 8
-    and 7."""
-    prob = Problem(3, 64, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
+    grid it fits from N = 128: kernel 8's launch count, and bitwise the state
+    of kernels 8 and 7; at N = 64 (three tiles) it makes one launch per pass."""
+    prob = Problem(3, 128, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
     st = random_state(prob, 2502_09537 + 311, 0.5)
     runs = [run(prob, st, [6], k) for k in (0, STREAM2, 7)]
     assert runs[0][2] == runs[1][2] == 6 / 2 + 3
@@ -84,6 +84,12 @@ def test_two_step_launches_are_the_default_for_fp32_3d():
     for r in runs[1:]:
         for x, y in zip(runs[0][0], r[0]):
             assert np.array_equal(x, y)
+    small = Problem(3, 64, 20.0, 1.0, 1.0, 1.0, 1.0, 5e-4)
+    st = random_state(small, 2502_09537 + 312, 0.5)
+    auto, pas = run(small, st, [6], 0), run(small, st, [6], 1)
+    assert auto[2] == pas[2]
+    for x, y in zip(auto[0], pas[0]):
+        assert np.array_equal(x, y)
 
 
 def test_two_step_launches_negative_kappa1_and_bumps():
